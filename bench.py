@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the Katsevich helical cone-beam reconstruction operator.
+
+One step = one full reconstruction (steps 1-7 of the paper's Section II) of
+the clinical workload: 512 x 512 x 256 volume at 1 mm, curved detector
+64 x 736, 1160 views/turn, 8 turns, maximal-fit pitch (70 mm), seeded random
+ellipsoid phantom (FP64 line integrals, stored FP32).  The metric is GUPS:
+voxel-view updates (each voxel's PI-window view count, summed) per second.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank reconstructs its own volume (independent
+problems, no collective on the data path: weak scaling) and rank 0 prints one
+JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Katsevich recon GUPS (voxel·views/s), vol/s, p50/p99 latency vs plain FP32"
+UNIT = "GUPS (1e9 voxel-view updates/s)"
+KERNELS_PER_STEP = 4  # deriv+rebin, Toeplitz GEMM, unrebin+cosine, backprojection
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(cfg_index, geom):
+    import numpy as np
+
+    import synth
+    cfg = synth.config(cfg_index)
+    ell = synth.phantom_for(cfg, geom, synth.phantom_seed(cfg_index))
+    sino = synth.project(geom, ell)
+    sino = synth.add_noise(sino, cfg["noise_sigma"], synth.noise_seed(cfg_index))
+    return cfg, sino.astype(np.float32)
+
+
+def describe(cfg, g, info, precision="fp32"):
+    return {"workload": cfg["name"], "volume_xyz": [g["nx"], g["ny"], g["nz"]], "voxel_mm": g["dx"],
+            "detector_rows_cols": [g["n_rows"], g["n_cols"]], "views": g["n_views"],
+            "views_per_turn": g["views_per_turn"], "pitch_mm": g["P"], "R_mm": g["R"], "D_mm": g["D"],
+            "slices_per_pitch": info["slices_per_pitch"], "n_psi": info["n_psi"],
+            "filtered_views": info["n_filtered_views"], "updates_per_volume": info["update_count"],
+            "precision": precision, "batch_per_gpu": 1,
+            "l2": "inputs larger than L2 (sinogram %.2f GB, filter workspace %.2f GB)" % (
+                g["n_views"] * g["n_rows"] * g["n_cols"] * 4 / 1e9, info["workspace_bytes"] / 1e9)}
+
+
+# --------------------------------------------------------------------------- oracle
+def oracle_sample(g, sino, info, n_views=96, n_vox=65536, seed=0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload and
+    extrapolate to one full reconstruction: filter time per view x filtered
+    views + backprojection time per update x update count."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    op = oracle.Plan(g, with_pi=False)
+    v0 = info["first_view"] + info["n_filtered_views"] // 2
+    t = time.perf_counter()
+    gF_part = op.filter(sino.astype(np.float64), v0, n_views)
+    t_filter = time.perf_counter() - t
+    s = g["nz"] // 2
+    ijk = np.stack([rng.integers(0, g["nx"], n_vox), rng.integers(0, g["ny"], n_vox), np.full(n_vox, s)], 1)
+    win = oracle.pi_windows(g, ijk)
+    a, b = int(win[0].min()), int(win[1].max())
+    gF = np.zeros((b - a + 1, g["n_rows"], g["n_cols"]))
+    k = min(n_views, gF.shape[0])
+    gF[:k] = gF_part[:k]
+    t = time.perf_counter()
+    oracle.backproject_points(g, gF, a, ijk, win)
+    t_bp = time.perf_counter() - t
+    upd = int((win[1] - win[0] + 1).sum())
+    est = t_filter / n_views * info["n_filtered_views"] + t_bp / upd * info["update_count"]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": info["update_count"] / est / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle (C, OpenMP) on {n_views} filtered views ({t_filter:.1f} s) and {n_vox} voxels "
+                      f"of slice {s} ({upd} updates, {t_bp:.1f} s), extrapolated to one full volume "
+                      f"({est:.0f} s)",
+            "seconds": t_filter + t_bp}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    cfg = synth.config(args.config)
+    g = oracle.derive_geometry(cfg)
+    # the oracle's own one-pitch table gives the update count and the filtered view window
+    t = oracle.pi_table(g)
+    N = oracle.pitch_slices(g)
+    s = list(range(g["nz"]))
+    upd = sum(int((t["k1"][j] - t["k0"][j] + 1).sum()) for j in (x % N for x in s))
+    kmin = min(int(t["k0"][x % N].min()) + (x // N) * g["views_per_turn"] for x in s)
+    kmax = max(int(t["k1"][x % N].max()) + (x // N) * g["views_per_turn"] for x in s)
+    info = {"first_view": kmin, "n_filtered_views": kmax - kmin + 1, "update_count": upd,
+            "slices_per_pitch": N, "n_psi": oracle.n_psi(g), "workspace_bytes": 0}
+    _, sino = workload(args.config, g)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(g, sino, info, n_views=16, n_vox=8192, seed=i)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    secs = sum(x["seconds"] for x in vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(cfg, g, info, "fp64"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_02309_b300 as kats
+    from paper_2201_02309_b300 import build as kbuild
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    kbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cfg = synth.config(args.config)
+    g = kats.make_geometry(cfg)
+    cfg, sino_np = workload(args.config, g)
+    plan = kats.Plan(g)
+    info = plan.info
+    sino = torch.from_numpy(sino_np).to(dev)
+    vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+    ws = plan.workspace(device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        plan.recon(sino, out=vol, workspace=ws)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.recon(sino, out=vol, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    updates = info["update_count"] * world
+    value = updates / (ms / 1e3) / 1e9
+
+    # per-kernel durations over the same work (events on the launching stream)
+    gF = torch.empty(plan.filtered_shape, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        ev[3 * i].record(stream)
+        kats.native.katsevich_filter(plan.handle, sino.data_ptr(), gF.data_ptr(), 1, 0, ws.data_ptr(), ws.numel(),
+                                     stream.cuda_stream)
+        ev[3 * i + 1].record(stream)
+        kats.native.katsevich_backproject(plan.handle, gF.data_ptr(), vol.data_ptr(), 1, stream.cuda_stream)
+        ev[3 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    t_filter = statistics.mean(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps))
+    t_bp = statistics.mean(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps))
+
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA
+    flop_per_update = 8.0  # bilinear interpolation (3 lerps) + weighted accumulate
+    achieved = info["update_count"] * flop_per_update / (t_bp / 1e3) / 1e12
+    roofline = {"kernel": "k_backproject", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 FMA issue: 148 SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz ({pk_kind} clock)",
+                "ms_per_launch": t_bp, "filter_ms": t_filter}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.from_numpy(sino_np).pin_memory()
+        hv = torch.empty(plan.vol_shape, dtype=torch.float32).pin_memory()
+        wsh = torch.empty(kats.native.katsevich_host_workspace_bytes(plan.handle, 1), dtype=torch.uint8, device=dev)
+        for _ in range(max(1, args.warmup)):
+            plan.recon_host(hs, hv, workspace=wsh)
+        barrier()
+        times = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            plan.recon_host(hs, hv, workspace=wsh)
+            times.append(time.perf_counter() - t)
+        te = max_over_ranks(statistics.mean(times))
+        h2d = (info["n_filtered_views"] + 1) * g["n_rows"] * g["n_cols"] * 4
+        e2e = {"value": updates / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": int(np.prod(plan.vol_shape)) * 4, "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(g, sino_np, info)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": describe(cfg, g, info), "vol_per_s": world / (ms / 1e3),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

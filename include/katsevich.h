@@ -1,0 +1,213 @@
+/*
+ * katsevich.h -- C ABI of the B300 (sm_103a) Katsevich helical cone-beam
+ * reconstruction library (curved detector, computed pitch by pitch).
+ *
+ * Operator (W. Wang et al., "A three-dimensional dual-domain deep network for
+ * high-pitch and sparse helical CT reconstruction", Sec. II):
+ *   steps 1-6  sinogram g -> filtered data g^F   (derivative, length weight,
+ *              forward rebinning onto kappa-lines, Hilbert transform in alpha,
+ *              backward rebinning, post-cosine weight)
+ *   step 7     g^F -> volume f by backprojection over each voxel's PI interval
+ * with the kappa tables and the PI tables of ONE pitch computed once per
+ * geometry (the "pre-calculating step") and reused for every pitch through the
+ * periodicity of the PI endpoints and of v*, alpha*, w*.
+ *
+ * Conventions shared by every entry point
+ *   helix     a(l) = (R cos(l+lambda0), R sin(l+lambda0), z0 + P l / (2 pi))
+ *   views     sinogram view k at l_k = lambda_first + k * 2 pi / views_per_turn
+ *   filtered  g^F view k at the half angle l_{k+1/2} (k = 0 .. n_views-2)
+ *   detector  column c at alpha_c = (c - (n_cols-1)/2) d_alpha + alpha_offset
+ *             row r at    w_r     = (r - (n_rows-1)/2) d_w     + w_offset
+ *             (curved detector at distance D; ray ~ D sin(a) e_u + D cos(a) e_v + w e_z)
+ *   volume    voxel (i, j, s) at (x0 + i dx, y0 + j dy, z_first + s dz)
+ *   layouts   sinogram [batch][n_views][n_rows][n_cols]   (float32, c fastest)
+ *             volume   [batch][nz][ny][nx]                (float32, x fastest)
+ *   pitch     P / dz must be an integer N (slices per pitch); slice s uses
+ *             PI-table slice s mod N shifted by (s div N) * views_per_turn views
+ *
+ * Memory: every data pointer is a DEVICE pointer on the current CUDA device
+ * unless the name says host.  The caller owns all buffers; the library only
+ * reads inputs and writes outputs.  A plan owns its device tables and is
+ * immutable after katsevich_plan returns, so one plan may be used from several
+ * streams at once (each call needs its own workspace).
+ *
+ * Errors: every entry point returns a KATS_* status; nothing throws across the
+ * ABI.  On a non-zero status, katsevich_last_error() returns a message for the
+ * calling thread, output buffers are not written by host-side checks, and a
+ * status of KATS_ECUDA means a CUDA call failed (its error string is in the
+ * message).
+ */
+#ifndef KATSEVICH_H
+#define KATSEVICH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KATS_API __attribute__((visibility("default")))
+#else
+#define KATS_API
+#endif
+
+#define KATS_OK 0
+#define KATS_EINVAL 1   /* bad argument: null pointer, size, dtype, batch      */
+#define KATS_EGEOM 2    /* invalid geometry (see katsevich_plan)               */
+#define KATS_ENOMEM 3   /* device allocation failed                            */
+#define KATS_ECUDA 4    /* a CUDA runtime/driver call failed                   */
+#define KATS_ETIMEOUT 5 /* a bounded wait gave up                               */
+#define KATS_ESPACE 6   /* caller workspace smaller than required              */
+
+/* Storage precision of the filtered data g^F (the derivative and Hilbert
+ * inputs follow it); arithmetic accumulates in FP32 in every mode. */
+#define KATS_PREC_FP32 0
+#define KATS_PREC_BF16 1
+#define KATS_PREC_FP16 2
+
+#define KATS_ENDPOINT_FRACTIONAL 0 /* midpoint rule: end views weighted by covered fraction */
+#define KATS_ENDPOINT_HARD 1       /* views with l_{k+1/2} in [lam_i, lam_o], weight 1     */
+
+typedef struct kats_geometry {
+    double R;            /* helix radius (mm), Sec. II helix equation                    */
+    double D;            /* source-to-detector distance (mm), curved detector            */
+    double P;            /* pitch (mm per turn)                                           */
+    double lambda0;      /* helix start angle (rad)                                       */
+    double z0;           /* helix start height (mm)                                       */
+    double lambda_first; /* angle of sinogram view 0 (rad)                                */
+    int64_t views_per_turn, n_views;
+    int64_t n_rows, n_cols;
+    double d_alpha, alpha_offset; /* column pitch and offset (rad)                        */
+    double d_w, w_offset;         /* row pitch and offset (mm at distance D)              */
+    int64_t nx, ny, nz;
+    double dx, dy, dz;            /* voxel size (mm)                                      */
+    double x0, y0, z_first;       /* centre of voxel (0, 0, 0) (mm)                       */
+    int64_t n_psi;                /* kappa lines; 0 selects 2 * n_rows                    */
+    int64_t endpoint_mode;        /* KATS_ENDPOINT_*                                      */
+    int64_t flags;                /* reserved, must be 0                                  */
+} kats_geometry;
+
+typedef struct kats_plan kats_plan; /* opaque; device-resident tables */
+
+typedef struct kats_plan_info {
+    /* Sec. II Eq. (maxvalue): lam_min/max over the PI endpoints of one pitch;
+     * alpha/w extremes of (alpha*, w*) over the views each voxel of that pitch
+     * backprojects (evaluated in FP32 on the device). */
+    double lambda_min, lambda_max, alpha_min, alpha_max, w_min, w_max;
+    double alpha_m;           /* arcsin(r_fov / R), r_fov = farthest volume corner   */
+    double psi_max;           /* pi/2 + alpha_m                                        */
+    int64_t slices_per_pitch; /* N = P / dz                                            */
+    int64_t n_psi;
+    int64_t first_view;       /* first filtered half-view the volume needs             */
+    int64_t n_filtered_views; /* filtered half-views needed (sinogram views: +1)       */
+    int64_t update_count;     /* sum over voxels of their PI-window view counts        */
+    int64_t workspace_bytes;  /* per concurrent call, FP32 storage                     */
+    int64_t plan_bytes;       /* device bytes held by the plan                         */
+} kats_plan_info;
+
+/*
+ * Largest pitch whose Tam-Danielsson window fits the detector rows, times
+ * `factor`, rounded down to a whole number of slices of thickness g->dz.
+ * (Sec. I: the row count needed for exact reconstruction grows with the pitch;
+ * on the curved detector the widest TD extent over |alpha| <= alpha_m is
+ * (D P / (2 pi R)) (pi/2 + alpha_m) / cos(alpha_m), which must not exceed the
+ * outermost row centre (n_rows - 1)/2 * d_w.)  Uses R, D, n_rows, d_w, dz and
+ * the volume extent of *g; g->P is ignored.  Host only.
+ */
+KATS_API int katsevich_fit_pitch(const kats_geometry *g, double factor, double *pitch_out);
+
+/*
+ * Pre-calculating step (Sec. II): validate *g and build, on the current
+ * device, in FP64 arithmetic,
+ *   - the forward-rebinning table w_kappa(alpha_{c+1/2}, psi_l) (Eq. (w_k)) as
+ *     (row index, weight), psi_l uniform on [-psi_max, psi_max];
+ *   - the backward-rebinning table psi_hat(alpha_c, w_r), the root of smallest
+ *     |psi| (Sec. II step 5), as (psi index, weight);
+ *   - the PI table of one pitch: PI-line endpoints lam_i < lam_o of every voxel
+ *     column point (x, y, z_first + j dz), j < N (Eq. (e1)), turned into the
+ *     first/last filtered view and their end weights.
+ * Errors: KATS_EGEOM when R, D, P, sizes or spacings are not positive, r_fov >=
+ * R, P/dz is not an integer, flags != 0, or some voxel's PI window needs a
+ * filtered view outside [0, n_views - 2]; KATS_ENOMEM / KATS_ECUDA otherwise.
+ * On success *out owns device memory until katsevich_plan_destroy.
+ * Synchronous (returns after the tables are built).
+ */
+KATS_API int katsevich_plan(const kats_geometry *g, kats_plan **out);
+
+/* Extents, sizes and the update count of a plan (host only). */
+KATS_API int katsevich_plan_info(const kats_plan *plan, kats_plan_info *info);
+
+/* Device workspace bytes one recon/adjoint call needs for `precision`. */
+KATS_API int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision);
+
+/*
+ * Full operator, steps 1-7 (Sec. II reconstruction step), for `batch`
+ * sinograms: sino [batch][n_views][n_rows][n_cols] -> vol [batch][nz][ny][nx].
+ * Only sinogram views [first_view, first_view + n_filtered_views] are read.
+ * `workspace` (device, >= katsevich_workspace_bytes) is scratch owned by the
+ * caller; `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Stream-ordered and asynchronous: returns after enqueueing the kernels.
+ */
+KATS_API int katsevich_recon(const kats_plan *plan, const float *sino, float *vol, int batch,
+                    int precision, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Exact transpose of katsevich_recon (same discretisation, same precision
+ * rule): vol_grad [batch][nz][ny][nx] -> sino_grad [batch][n_views][n_rows][n_cols].
+ * Every element of sino_grad is written (views outside the window get 0).
+ */
+KATS_API int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, float *sino_grad, int batch,
+                      int precision, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Steps 1-6 only (Sec. II Eqs. (Deriv), (LW), (FR), (HF), (BR), (PW)):
+ * sino [batch][n_views][n_rows][n_cols] -> gF [batch][n_filtered_views][n_rows][n_cols],
+ * filtered view v of the output is half-view first_view + v.
+ */
+KATS_API int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int batch,
+                     int precision, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Step 7 only (Sec. II backprojection step): gF [batch][n_filtered_views][n_rows][n_cols]
+ * (layout of katsevich_filter's output, FP32) -> vol [batch][nz][ny][nx].
+ */
+KATS_API int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, int batch, void *stream);
+
+/*
+ * End-to-end call with HOST buffers: copies the needed sinogram views from
+ * host_sino (pinned memory recommended) to the device, runs katsevich_recon and
+ * copies the volume back to host_vol, all on `stream`, then waits for the
+ * stream.  `workspace` (device) must hold katsevich_host_workspace_bytes.
+ */
+KATS_API int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision);
+KATS_API int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch,
+                         int precision, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Copy a plan table to host memory (for checks against an independent
+ * implementation).  which: 0 kappa row index (int32 [n_psi][n_cols-1]),
+ * 1 kappa weight (float), 2 psi index (int32 [n_rows][n_cols]), 3 psi weight
+ * (float), 4 first view k0 (int32 [N][ny][nx]), 5 last view k1, 6 first-view
+ * weight (float), 7 last-view weight (float).  `bytes` must equal the size.
+ */
+KATS_API int katsevich_plan_table(const kats_plan *plan, int which, void *host_dst, size_t bytes);
+
+/*
+ * The device FP64 PI-line solver on n host points xyz[n][3] (Eq. (e1)):
+ * writes lam_i[n], lam_o[n] (host).  Synchronous; for checks.
+ */
+KATS_API int katsevich_pi_endpoints(const kats_geometry *g, int64_t n, const double *host_xyz,
+                           double *host_lam_i, double *host_lam_o);
+
+/* Release a plan's device memory.  NULL is allowed. */
+KATS_API void katsevich_plan_destroy(kats_plan *plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+KATS_API const char *katsevich_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KATSEVICH_H */

@@ -375,10 +375,20 @@ void or_forward_rebin(const or_geom *g, const int32_t *kidx, const double *kfrac
  * alpha_c - alpha_{c'+1/2} = (c - c' - 1/2) d_alpha; never singular.
  * g3 [nv][n_psi][Nc-1] -> g4 [nv][n_psi][Nc].
  */
+/* kernel value d_alpha / (pi sin((n - 1/2) d_alpha)) for n = c - c', stored at n + nc - 2 */
+static double *hilbert_kernel(const or_geom *g)
+{
+    const int64_t nc = g->n_cols;
+    double *hk = malloc(sizeof(double) * (size_t)(2 * nc - 2));
+    for (int64_t n = -(nc - 2); n <= nc - 1; ++n)
+        hk[n + nc - 2] = g->d_alpha / (M_PI * sin(((double)n - 0.5) * g->d_alpha));
+    return hk;
+}
+
 void or_hilbert(const or_geom *g, const double *g3, int64_t nv, double *g4)
 {
     const int64_t nc = g->n_cols, nc1 = nc - 1, np = n_psi(g);
-    const double da = g->d_alpha;
+    double *hk = hilbert_kernel(g);
 #pragma omp parallel for collapse(2)
     for (int64_t k = 0; k < nv; ++k)
         for (int64_t l = 0; l < np; ++l) {
@@ -386,11 +396,11 @@ void or_hilbert(const or_geom *g, const double *g3, int64_t nv, double *g4)
             double *out = g4 + (k * np + l) * nc;
             for (int64_t c = 0; c < nc; ++c) {
                 double acc = 0.0;
-                for (int64_t cp = 0; cp < nc1; ++cp)
-                    acc += da * in[cp] / (M_PI * sin(((double)(c - cp) - 0.5) * da));
+                for (int64_t cp = 0; cp < nc1; ++cp) acc += hk[c - cp + nc - 2] * in[cp];
                 out[c] = acc;
             }
         }
+    free(hk);
 }
 
 /*
@@ -648,6 +658,7 @@ void or_filter_adjoint(const or_geom *g, const int32_t *kidx, const double *kfra
 {
     const int64_t nr = g->n_rows, nc = g->n_cols, nc1 = nc - 1, np = n_psi(g);
     const double da = g->d_alpha;
+    double *hk = hilbert_kernel(g);
     double *g1 = calloc((size_t)(nv * nr * nc1), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < nv; ++k) {
@@ -666,8 +677,7 @@ void or_filter_adjoint(const or_geom *g, const int32_t *kidx, const double *kfra
         for (int64_t l = 0; l < np; ++l)
             for (int64_t cp = 0; cp < nc1; ++cp) {
                 double acc = 0.0;
-                for (int64_t c = 0; c < nc; ++c)
-                    acc += da * g4[l * nc + c] / (M_PI * sin(((double)(c - cp) - 0.5) * da));
+                for (int64_t c = 0; c < nc; ++c) acc += hk[c - cp + nc - 2] * g4[l * nc + c];
                 g3[l * nc1 + cp] = acc;
             }
         /* step 3^T: scatter psi lines back to detector rows */
@@ -706,6 +716,7 @@ void or_filter_adjoint(const or_geom *g, const int32_t *kidx, const double *kfra
                 sino[(k * nr + r) * nc + c] = acc;
             }
     free(g1);
+    free(hk);
 }
 
 /* ---------------------------------------------------------------- extents */

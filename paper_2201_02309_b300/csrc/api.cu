@@ -1,0 +1,183 @@
+// C-ABI entry points of the reconstruction step (Sec. II): steps 1-6 then 7,
+// their transposes, and the host-buffer variant.
+#include <algorithm>
+
+#include "common.cuh"
+
+using namespace kats;
+
+namespace {
+
+size_t gf_bytes(const Plan &p) { return sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.g.n_cols); }
+size_t sino_item(const Plan &p) { return (size_t)(p.g.n_views * p.g.n_rows * p.g.n_cols); }
+size_t vol_item(const Plan &p) { return (size_t)(p.g.nx * p.g.ny * p.g.nz); }
+size_t view_elems(const Plan &p) { return (size_t)(p.g.n_rows * p.g.n_cols); }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+int check_common(const kats_plan *plan, const void *in, const void *out, int batch, int precision, const void *ws)
+{
+    if (!plan || !in || !out) {
+        set_error("null plan or buffer");
+        return KATS_EINVAL;
+    }
+    if (batch < 1) {
+        set_error("batch must be >= 1 (got %d)", batch);
+        return KATS_EINVAL;
+    }
+    if (precision != KATS_PREC_FP32) {
+        set_error("precision %d is not available in this build", precision);
+        return KATS_EINVAL;
+    }
+    if (!ws) {
+        set_error("null workspace");
+        return KATS_EINVAL;
+    }
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) {
+        set_error("plan was built on device %d, current device is %d", p->device, dev);
+        return KATS_EINVAL;
+    }
+    return KATS_OK;
+}
+
+size_t recon_ws(const Plan &p) { return align256(gf_bytes(p)) + filter_workspace_bytes(p); }
+size_t adjoint_ws(const Plan &p) { return align256(gf_bytes(p)) + filter_adjoint_workspace_bytes(p); }
+
+}  // namespace
+
+extern "C" {
+
+int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision)
+{
+    if (!plan || precision != KATS_PREC_FP32) return -1;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    return (int64_t)std::max(recon_ws(p), adjoint_ws(p));
+}
+
+int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int batch, int precision, void *workspace,
+                     size_t workspace_bytes, void *stream)
+{
+    int rc = check_common(plan, sino, gF, batch, precision, workspace);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    if (workspace_bytes < filter_workspace_bytes(p)) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, filter_workspace_bytes(p));
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b = 0; b < batch; ++b) {
+        rc = launch_filter(p, sino + b * sino_item(p) + p.first_view * view_elems(p), gF + b * p.n_fviews * view_elems(p),
+                           workspace, workspace_bytes, st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
+int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, int batch, void *stream)
+{
+    if (!plan || !gF || !vol || batch < 1) {
+        set_error("bad argument");
+        return KATS_EINVAL;
+    }
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b = 0; b < batch; ++b) {
+        int rc = launch_backproject(p, gF + b * p.n_fviews * view_elems(p), vol + b * vol_item(p), st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
+int katsevich_recon(const kats_plan *plan, const float *sino, float *vol, int batch, int precision, void *workspace,
+                    size_t workspace_bytes, void *stream)
+{
+    int rc = check_common(plan, sino, vol, batch, precision, workspace);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    if (workspace_bytes < recon_ws(p)) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, recon_ws(p));
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float *gF = (float *)workspace;
+    char *fws = (char *)workspace + align256(gf_bytes(p));
+    const size_t fws_bytes = workspace_bytes - align256(gf_bytes(p));
+    for (int b = 0; b < batch; ++b) {
+        rc = launch_filter(p, sino + b * sino_item(p) + p.first_view * view_elems(p), gF, fws, fws_bytes, st);
+        if (rc) return rc;
+        rc = launch_backproject(p, gF, vol + b * vol_item(p), st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
+int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, float *sino_grad, int batch, int precision,
+                      void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = check_common(plan, vol_grad, sino_grad, batch, precision, workspace);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    if (workspace_bytes < adjoint_ws(p)) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, adjoint_ws(p));
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float *gF = (float *)workspace;
+    char *fws = (char *)workspace + align256(gf_bytes(p));
+    const size_t fws_bytes = workspace_bytes - align256(gf_bytes(p));
+    for (int b = 0; b < batch; ++b) {
+        rc = launch_backproject_adjoint(p, vol_grad + b * vol_item(p), gF, st);
+        if (rc) return rc;
+        rc = launch_filter_adjoint(p, gF, sino_grad + b * sino_item(p), fws, fws_bytes, st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
+int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision)
+{
+    if (!plan || batch < 1 || precision != KATS_PREC_FP32) return -1;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
+    return (int64_t)(align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws(p));
+}
+
+int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch, int precision,
+                         void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = check_common(plan, host_sino, host_vol, batch, precision, workspace);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    const int64_t need = katsevich_host_workspace_bytes(plan, batch, precision);
+    if ((int64_t)workspace_bytes < need) {
+        set_error("workspace %zu < %lld bytes", workspace_bytes, (long long)need);
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
+    float *d_win = (float *)workspace;
+    float *d_vol = (float *)((char *)workspace + align256(win));
+    char *rws = (char *)d_vol + align256(sizeof(float) * vol_item(p));
+    const size_t rws_bytes = recon_ws(p);
+    float *gF = (float *)rws;
+    char *fws = rws + align256(gf_bytes(p));
+    const size_t fws_bytes = rws_bytes - align256(gf_bytes(p));
+    for (int b = 0; b < batch; ++b) {
+        KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + b * sino_item(p) + p.first_view * view_elems(p), win,
+                                  cudaMemcpyHostToDevice, st));
+        rc = launch_filter(p, d_win, gF, fws, fws_bytes, st);
+        if (rc) return rc;
+        rc = launch_backproject(p, gF, d_vol, st);
+        if (rc) return rc;
+        KATS_CUDA(cudaMemcpyAsync(host_vol + b * vol_item(p), d_vol, sizeof(float) * vol_item(p),
+                                  cudaMemcpyDeviceToHost, st));
+    }
+    KATS_CUDA(cudaStreamSynchronize(st));
+    return KATS_OK;
+}
+
+}  // extern "C"

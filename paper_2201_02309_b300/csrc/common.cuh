@@ -1,0 +1,65 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "../../include/katsevich.h"
+
+namespace kats {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Device-resident plan: the pre-calculated tables of one pitch (Sec. II).
+struct Plan {
+    kats_geometry g;
+    int device;
+    // derived scalars (FP64, host)
+    int64_t N;        // slices per pitch
+    int64_t n_psi;    // kappa lines
+    int64_t nc1;      // half-grid columns (n_cols - 1)
+    double alpha_m, psi_max, dpsi, h, dlam;
+    int64_t first_view, n_fviews;  // filtered half-views the volume needs
+    int64_t update_count;
+    double ext[6];
+    // device tables
+    int32_t *kap_idx = nullptr;  // [n_psi][nc1] floor of the fractional row
+    float *kap_frac = nullptr;   // [n_psi][nc1]
+    int32_t *psi_idx = nullptr;  // [n_rows][n_cols] floor of the fractional psi index, -2 = no root
+    float *psi_frac = nullptr;   // [n_rows][n_cols]
+    int32_t *pi_k0 = nullptr, *pi_k1 = nullptr;  // [N][ny][nx]
+    float *pi_w0 = nullptr, *pi_w1 = nullptr;    // [N][ny][nx]
+    int32_t *slice_kmin = nullptr, *slice_kmax = nullptr;  // [N] per table slice
+    float *hk = nullptr;    // Hilbert kernel, [2 n_cols - 2], entry n + n_cols - 2 for n = c - c'
+    float *lw = nullptr;    // [n_rows] length-correction weight
+    float *cosa = nullptr;  // [n_cols] cos(alpha_c)
+    float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
+    size_t plan_bytes = 0;
+};
+
+// thread-local error message
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define KATS_CUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::kats::cuda_fail(_e, #call);     \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Kernel launchers (defined in filter.cu, backproject.cu, adjoint.cu).
+// sino points at sinogram view p.first_view; gF receives p.n_fviews filtered views
+int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st);
+int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st);
+int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaStream_t st);
+int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes,
+                          cudaStream_t st);
+size_t filter_workspace_bytes(const Plan &p);
+size_t filter_adjoint_workspace_bytes(const Plan &p);
+
+}  // namespace kats

@@ -1,0 +1,317 @@
+// Steps 1-6 of the reconstruction step (Sec. II): sinogram -> filtered data g^F.
+//
+//   k_deriv_rebin   steps 1-3: derivative at constant direction (Eq. (Deriv)) on
+//                   the half grid, length weight (Eq. (LW)), forward height
+//                   rebinning onto kappa-lines (Eq. (FR)) -> g3 [v][psi][Kp]
+//   k_toeplitz_gemm step 4: Hilbert transform in alpha at constant psi
+//                   (Eq. (HF)) as a Toeplitz contraction g4 = g3 . T,
+//                   T[c'][c] = d_alpha / (pi sin((c - c' - 1/2) d_alpha))
+//   k_unrebin_cos   steps 5-6: backward height rebinning (Eq. (BR)) and the
+//                   post-cosine weight (Eq. (PW)) -> g^F [v][row][col]
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace kats {
+
+// Padded K extent of the g3 rows (multiple of 16 floats, zero tail).
+static inline int64_t kpad(const Plan &p) { return (p.nc1 + 15) / 16 * 16; }
+
+size_t filter_workspace_bytes(const Plan &p)
+{
+    const int64_t nv = p.n_fviews;
+    return sizeof(float) * (size_t)(nv * p.n_psi * kpad(p) + nv * p.n_psi * p.g.n_cols);
+}
+
+// ---------------------------------------------------------------- steps 1-3
+// grid (ceil(Kp / 32), n_fviews); block 256; dynamic smem n_rows * 32 floats.
+__global__ void k_deriv_rebin(const float *__restrict__ sino, float *__restrict__ g3, const int32_t *__restrict__ kap_idx,
+                              const float *__restrict__ kap_frac, const float *__restrict__ lw, int nv, int n_rows, int n_cols, int n_psi, int Kp, float a_lam, float a_alp)
+{
+    extern __shared__ float s_g2[];  // [n_rows][32]
+    const int nc1 = n_cols - 1;
+    const int c0 = blockIdx.x * 32;
+    const int cc = threadIdx.x & 31;
+    const int c = c0 + cc;
+    for (int v = blockIdx.y; v < nv; v += gridDim.y) {
+    const float *p0 = sino + (int64_t)v * n_rows * n_cols;  // sino points at sinogram view first_view
+    const float *p1 = p0 + (int64_t)n_rows * n_cols;
+    __syncthreads();  // s_g2 of the previous view fully consumed
+    for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) {
+        float val = 0.0f;
+        if (c < nc1) {
+            const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
+            const float d = p1[r * n_cols + c], e = p1[r * n_cols + c + 1];
+            // (dg/dlambda + dg/dalpha) at the cell centre, times D / sqrt(D^2 + w^2)
+            val = lw[r] * (a_lam * ((d - a) + (e - b)) + a_alp * ((b - a) + (e - d)));
+        }
+        s_g2[r * 32 + cc] = val;
+    }
+    __syncthreads();
+    float *out = g3 + (int64_t)v * n_psi * Kp;
+    for (int l = threadIdx.x >> 5; l < n_psi; l += blockDim.x >> 5) {
+        float val = 0.0f;
+        if (c < nc1) {
+            const int r = kap_idx[l * nc1 + c];
+            const float f = kap_frac[l * nc1 + c];
+            const float lo = (r >= 0 && r < n_rows) ? s_g2[r * 32 + cc] : 0.0f;
+            const float hi = (r + 1 >= 0 && r + 1 < n_rows) ? s_g2[(r + 1) * 32 + cc] : 0.0f;
+            val = (1.0f - f) * lo + f * hi;
+        }
+        if (c < Kp) out[(int64_t)l * Kp + c] = val;
+    }
+    }
+}
+
+// ---------------------------------------------------------------- step 4
+// C[m][n] = sum_k A[m][k] * T(k, n), T from the 1-D kernel hk:
+//   forward   (transpose = 0): k = c' < nc1, n = c < nc, T = hk[n - k + nc - 2]
+//   transpose (transpose = 1): k = c < nc,   n = c' < nc1, T = hk[k - n + nc - 2]
+// A is [M][lda] (row-major, zero beyond the valid K), C is [M][ldc].
+constexpr int GBM = 128, GBN = 128, GBK = 16;
+
+__global__ void __launch_bounds__(256) k_toeplitz_gemm(const float *__restrict__ A, float *__restrict__ C,
+                                                       const float *__restrict__ hk, int64_t M, int K, int Nn,
+                                                       int lda, int ldc, int nc, int transpose)
+{
+    __shared__ float As[GBK][GBM + 4];
+    __shared__ float Bs[GBK][GBN + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * GBM;
+    const int n0 = blockIdx.x * GBN;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        // A tile: 128 rows x 16 k -> As[k][m]
+        for (int e = tid; e < GBM * GBK; e += 256) {
+            const int mm = e / GBK, kk = e % GBK;
+            const int64_t m = m0 + mm;
+            const int k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? A[m * lda + k] : 0.0f;
+        }
+        // B tile generated from the Toeplitz kernel
+        for (int e = tid; e < GBN * GBK; e += 256) {
+            const int kk = e / GBN, nn = e % GBN;
+            const int k = k0 + kk, n = n0 + nn;
+            float t = 0.0f;
+            if (k < K && n < Nn) t = transpose ? hk[k - n + nc - 2] : hk[n - k + nc - 2];
+            Bs[kk][nn] = t;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            float a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                a[i + 4] = As[kk][64 + ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+                b[i + 4] = Bs[kk][64 + tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (n < ldc) C[m * ldc + n] = (n < Nn) ? acc[i][j] : 0.0f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- steps 5-6
+__global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ gF, const int32_t *__restrict__ psi_idx,
+                              const float *__restrict__ psi_frac, const float *__restrict__ cosa, int64_t nv,
+                              int n_rows, int n_cols, int n_psi)
+{
+    const int64_t per = (int64_t)n_rows * n_cols;
+    const int64_t total = nv * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / per;
+        const int rc = (int)(t % per);
+        const int c = rc % n_cols;
+        const int l = psi_idx[rc];
+        const float f = psi_frac[rc];
+        const float *col = g4 + v * n_psi * n_cols + c;
+        const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * n_cols] : 0.0f;
+        const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * n_cols] : 0.0f;
+        gF[t] = cosa[c] * ((1.0f - f) * lo + f * hi);
+    }
+}
+
+int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const int64_t nv = p.n_fviews, Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
+    if (ws_bytes < filter_workspace_bytes(p)) {
+        set_error("filter workspace too small: %zu < %zu", ws_bytes, filter_workspace_bytes(p));
+        return KATS_ESPACE;
+    }
+    float *g3 = (float *)ws;
+    float *g4 = g3 + nv * np * Kp;
+    const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
+    const size_t smem = sizeof(float) * 32 * (size_t)nr;
+    if (smem > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_deriv_rebin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 g1((unsigned)ceil_div(Kp, 32), (unsigned)std::min<int64_t>(nv, 65535));
+    k_deriv_rebin<<<g1, 256, smem, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc,
+                                         (int)np, (int)Kp, a_lam, a_alp);
+    KATS_CUDA(cudaGetLastError());
+    const int64_t M = nv * np;
+    if (ceil_div(M, GBM) > 65535) {
+        set_error("too many filtered views for one launch (%lld)", (long long)nv);
+        return KATS_EINVAL;
+    }
+    dim3 g2((unsigned)ceil_div(nc, GBN), (unsigned)ceil_div(M, GBM));
+    k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, (int)nc, (int)nc, 0);
+    KATS_CUDA(cudaGetLastError());
+    const int64_t total = nv * nr * nc;
+    k_unrebin_cos<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
+        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np);
+    KATS_CUDA(cudaGetLastError());
+    return KATS_OK;
+}
+
+// ------------------------------------------------------------ transposes
+size_t filter_adjoint_workspace_bytes(const Plan &p)
+{
+    const int64_t nv = p.n_fviews;
+    // region 1: g4^T [v][psi][Kp4], later reused for g1^T [v][row][nc1]; region 2: g3^T [v][psi][Kp]
+    const int64_t Kp4 = (p.g.n_cols + 15) / 16 * 16;
+    const int64_t r1 = std::max<int64_t>(p.n_psi * Kp4, p.g.n_rows * p.nc1);
+    return sizeof(float) * (size_t)(nv * r1 + nv * p.n_psi * kpad(p));
+}
+
+// 6^T then 5^T: g4a[v][l][c] = sum_r cos(alpha_c) gF[v][r][c] * (tap weight of l)
+// grid (ceil(nc / 32), nv); block 256; smem n_psi * 32 floats.
+__global__ void k_unrebin_cos_T(const float *__restrict__ gF, float *__restrict__ g4a, const int32_t *__restrict__ psi_idx,
+                                const float *__restrict__ psi_frac, const float *__restrict__ cosa, int nv,
+                                int n_rows, int n_cols, int n_psi, int ld4)
+{
+    extern __shared__ float s[];  // [n_psi][32]
+    const int c0 = blockIdx.x * 32, cc = threadIdx.x & 31, c = c0 + cc;
+    for (int v = blockIdx.y; v < nv; v += gridDim.y) {
+    __syncthreads();  // previous view's results written out
+    for (int e = threadIdx.x; e < n_psi * 32; e += blockDim.x) s[e] = 0.0f;
+    __syncthreads();
+    if (c < n_cols) {
+        const float *in = gF + (int64_t)v * n_rows * n_cols;
+        for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) {
+            const int rc = r * n_cols + c;
+            const float val = cosa[c] * in[rc];
+            const int l = psi_idx[rc];
+            const float f = psi_frac[rc];
+            if (l >= 0 && l < n_psi) atomicAdd(&s[l * 32 + cc], (1.0f - f) * val);
+            if (l + 1 >= 0 && l + 1 < n_psi) atomicAdd(&s[(l + 1) * 32 + cc], f * val);
+        }
+    }
+    __syncthreads();
+    float *out = g4a + (int64_t)v * n_psi * ld4;
+    for (int l = threadIdx.x >> 5; l < n_psi; l += blockDim.x >> 5)
+        if (c < ld4) out[(int64_t)l * ld4 + c] = (c < n_cols) ? s[l * 32 + cc] : 0.0f;
+    }
+}
+
+// 3^T then 2^T: g1a[v][r][c'] = lw[r] * sum_l (tap weight of r) g3a[v][l][c']
+__global__ void k_rebin_T(const float *__restrict__ g3a, float *__restrict__ g1a, const int32_t *__restrict__ kap_idx,
+                          const float *__restrict__ kap_frac, const float *__restrict__ lw, int nv, int n_rows,
+                          int n_cols, int n_psi, int Kp)
+{
+    extern __shared__ float s[];  // [n_rows][32]
+    const int nc1 = n_cols - 1;
+    const int c0 = blockIdx.x * 32, cc = threadIdx.x & 31, c = c0 + cc;
+    for (int v = blockIdx.y; v < nv; v += gridDim.y) {
+    __syncthreads();  // previous view's results written out
+    for (int e = threadIdx.x; e < n_rows * 32; e += blockDim.x) s[e] = 0.0f;
+    __syncthreads();
+    if (c < nc1) {
+        const float *in = g3a + (int64_t)v * n_psi * Kp;
+        for (int l = threadIdx.x >> 5; l < n_psi; l += blockDim.x >> 5) {
+            const float val = in[(int64_t)l * Kp + c];
+            const int r = kap_idx[l * nc1 + c];
+            const float f = kap_frac[l * nc1 + c];
+            if (r >= 0 && r < n_rows) atomicAdd(&s[r * 32 + cc], (1.0f - f) * val);
+            if (r + 1 >= 0 && r + 1 < n_rows) atomicAdd(&s[(r + 1) * 32 + cc], f * val);
+        }
+    }
+    __syncthreads();
+    if (c < nc1) {
+        float *out = g1a + (int64_t)v * n_rows * nc1;
+        for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) out[r * nc1 + c] = lw[r] * s[r * 32 + cc];
+    }
+    }
+}
+
+// 1^T: each sample gathers the (up to) four half-grid cells that read it.
+__global__ void k_deriv_T(const float *__restrict__ g1a, float *__restrict__ sino, int64_t first_view, int64_t nv,
+                          int64_t n_views, int n_rows, int n_cols, float a_lam, float a_alp)
+{
+    const int nc1 = n_cols - 1;
+    const int64_t per = (int64_t)n_rows * n_cols, total = n_views * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / per;
+        const int rc = (int)(t % per), r = rc / n_cols, c = rc % n_cols;
+        float acc = 0.0f;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int dc = 0; dc < 2; ++dc) {
+                const int64_t kp = k - dk - first_view;
+                const int cp = c - dc;
+                if (kp < 0 || kp >= nv || cp < 0 || cp >= nc1) continue;
+                const float coef = (dk ? a_lam : -a_lam) + (dc ? a_alp : -a_alp);
+                acc = fmaf(coef, g1a[(kp * n_rows + r) * nc1 + cp], acc);
+            }
+        sino[t] = acc;
+    }
+}
+
+int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const int64_t nv = p.n_fviews, Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
+    const int64_t Kp4 = (nc + 15) / 16 * 16;
+    if (ws_bytes < filter_adjoint_workspace_bytes(p)) {
+        set_error("filter adjoint workspace too small");
+        return KATS_ESPACE;
+    }
+    const int64_t r1 = std::max<int64_t>(np * Kp4, nr * p.nc1);
+    float *g4a = (float *)ws;
+    float *g3a = g4a + nv * r1;
+    float *g1a = g4a;  // g4^T is dead once g3^T is formed
+    size_t sm1 = sizeof(float) * 32 * (size_t)np, sm2 = sizeof(float) * 32 * (size_t)nr;
+    if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_unrebin_cos_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    if (sm2 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_rebin_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    k_unrebin_cos_T<<<dim3((unsigned)ceil_div(Kp4, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm1, st>>>(
+        gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp4);
+    KATS_CUDA(cudaGetLastError());
+    const int64_t M = nv * np;
+    if (ceil_div(M, GBM) > 65535) {
+        set_error("too many filtered views for one launch (%lld)", (long long)nv);
+        return KATS_EINVAL;
+    }
+    k_toeplitz_gemm<<<dim3((unsigned)ceil_div(p.nc1, GBN), (unsigned)ceil_div(M, GBM)), 256, 0, st>>>(
+        g4a, g3a, p.hk, M, (int)nc, (int)p.nc1, (int)Kp4, (int)Kp, (int)nc, 1);
+    KATS_CUDA(cudaGetLastError());
+    k_rebin_T<<<dim3((unsigned)ceil_div(p.nc1, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm2, st>>>(
+        g3a, g1a, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp);
+    KATS_CUDA(cudaGetLastError());
+    const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
+    const int64_t total = p.g.n_views * nr * nc;
+    k_deriv_T<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
+        g1a, sino, p.first_view, nv, p.g.n_views, (int)nr, (int)nc, a_lam, a_alp);
+    KATS_CUDA(cudaGetLastError());
+    return KATS_OK;
+}
+
+}  // namespace kats

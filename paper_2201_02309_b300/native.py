@@ -1,0 +1,174 @@
+"""ctypes binding of libkatsevich.so: the C-ABI entry points under the same
+names, argument marshalling only.  Every step of the operator runs in the
+library's CUDA kernels; nothing here computes on the host."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libkatsevich.so")
+
+KATS_OK, KATS_EINVAL, KATS_EGEOM, KATS_ENOMEM, KATS_ECUDA, KATS_ETIMEOUT, KATS_ESPACE = range(7)
+KATS_PREC_FP32, KATS_PREC_BF16, KATS_PREC_FP16 = 0, 1, 2
+KATS_ENDPOINT_FRACTIONAL, KATS_ENDPOINT_HARD = 0, 1
+
+_STATUS = {1: "KATS_EINVAL", 2: "KATS_EGEOM", 3: "KATS_ENOMEM", 4: "KATS_ECUDA", 5: "KATS_ETIMEOUT", 6: "KATS_ESPACE"}
+
+# Every symbol include/katsevich.h declares.
+EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "katsevich_workspace_bytes",
+           "katsevich_recon", "katsevich_adjoint", "katsevich_filter", "katsevich_backproject",
+           "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
+           "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error"]
+
+
+class kats_geometry(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("D", ctypes.c_double), ("P", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("z0", ctypes.c_double), ("lambda_first", ctypes.c_double),
+                ("views_per_turn", ctypes.c_int64), ("n_views", ctypes.c_int64),
+                ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("d_alpha", ctypes.c_double), ("alpha_offset", ctypes.c_double),
+                ("d_w", ctypes.c_double), ("w_offset", ctypes.c_double),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z_first", ctypes.c_double),
+                ("n_psi", ctypes.c_int64), ("endpoint_mode", ctypes.c_int64), ("flags", ctypes.c_int64)]
+
+
+class kats_plan_info(ctypes.Structure):
+    _fields_ = [("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
+                ("w_min", ctypes.c_double), ("w_max", ctypes.c_double),
+                ("alpha_m", ctypes.c_double), ("psi_max", ctypes.c_double),
+                ("slices_per_pitch", ctypes.c_int64), ("n_psi", ctypes.c_int64),
+                ("first_view", ctypes.c_int64), ("n_filtered_views", ctypes.c_int64),
+                ("update_count", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("plan_bytes", ctypes.c_int64)]
+
+
+class KatsevichError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree CUDA library; fail loudly when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libkatsevich.so is missing at {LIB_PATH}; run paper_2201_02309_b300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    sig = {
+        "katsevich_fit_pitch": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_double)]),
+        "katsevich_plan": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.POINTER(P)]),
+        "katsevich_plan_info": (ctypes.c_int, [P, ctypes.POINTER(kats_plan_info)]),
+        "katsevich_workspace_bytes": (ctypes.c_int64, [P, ctypes.c_int]),
+        "katsevich_recon": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "katsevich_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "katsevich_filter": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "katsevich_backproject": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "katsevich_host_workspace_bytes": (ctypes.c_int64, [P, ctypes.c_int, ctypes.c_int]),
+        "katsevich_recon_host": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "katsevich_plan_table": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_size_t]),
+        "katsevich_pi_endpoints": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_int64, P, P, P]),
+        "katsevich_plan_destroy": (None, [P]),
+        "katsevich_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int) -> None:
+    if status != KATS_OK:
+        msg = load().katsevich_last_error().decode(errors="replace")
+        raise KatsevichError(status, msg)
+
+
+def geometry_struct(geom: dict) -> kats_geometry:
+    vals = {k: geom.get(k, 0) for k, _ in kats_geometry._fields_}
+    return kats_geometry(**vals)
+
+
+# --- same names as the C ABI -------------------------------------------------
+def katsevich_fit_pitch(geom: dict, factor: float = 1.0) -> float:
+    out = ctypes.c_double()
+    g = geometry_struct(geom)
+    check(load().katsevich_fit_pitch(ctypes.byref(g), factor, ctypes.byref(out)))
+    return out.value
+
+
+def katsevich_plan(geom: dict) -> int:
+    g = geometry_struct(geom)
+    h = ctypes.c_void_p()
+    check(load().katsevich_plan(ctypes.byref(g), ctypes.byref(h)))
+    return h.value
+
+
+def katsevich_plan_info(plan: int) -> dict:
+    info = kats_plan_info()
+    check(load().katsevich_plan_info(plan, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in kats_plan_info._fields_}
+
+
+def katsevich_workspace_bytes(plan: int, precision: int = KATS_PREC_FP32) -> int:
+    n = load().katsevich_workspace_bytes(plan, precision)
+    if n < 0:
+        raise KatsevichError(KATS_EINVAL, "workspace size unavailable for this precision")
+    return n
+
+
+def katsevich_recon(plan, sino_ptr, vol_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_recon(plan, sino_ptr, vol_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr))
+
+
+def katsevich_adjoint(plan, vol_ptr, sino_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_adjoint(plan, vol_ptr, sino_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr))
+
+
+def katsevich_filter(plan, sino_ptr, gF_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_filter(plan, sino_ptr, gF_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr))
+
+
+def katsevich_backproject(plan, gF_ptr, vol_ptr, batch, stream_ptr) -> None:
+    check(load().katsevich_backproject(plan, gF_ptr, vol_ptr, batch, stream_ptr))
+
+
+def katsevich_host_workspace_bytes(plan, batch, precision=KATS_PREC_FP32) -> int:
+    n = load().katsevich_host_workspace_bytes(plan, batch, precision)
+    if n < 0:
+        raise KatsevichError(KATS_EINVAL, "host workspace size unavailable")
+    return n
+
+
+def katsevich_recon_host(plan, host_sino_ptr, host_vol_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_recon_host(plan, host_sino_ptr, host_vol_ptr, batch, precision, ws_ptr, ws_bytes,
+                                      stream_ptr))
+
+
+def katsevich_plan_table(plan, which, dst_ptr, nbytes) -> None:
+    check(load().katsevich_plan_table(plan, which, dst_ptr, nbytes))
+
+
+def katsevich_pi_endpoints(geom: dict, n, xyz_ptr, li_ptr, lo_ptr) -> None:
+    g = geometry_struct(geom)
+    check(load().katsevich_pi_endpoints(ctypes.byref(g), n, xyz_ptr, li_ptr, lo_ptr))
+
+
+def katsevich_plan_destroy(plan) -> None:
+    load().katsevich_plan_destroy(plan)
+
+
+def katsevich_last_error() -> str:
+    return load().katsevich_last_error().decode(errors="replace")

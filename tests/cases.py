@@ -1,0 +1,55 @@
+"""Workload builders shared by the parity tests (geometry from the oracle's own
+derivation, inputs from the seeded generator)."""
+import math
+
+import numpy as np
+
+import oracle
+import synth
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def c1_case():
+    cfg = synth.config(1)
+    g = oracle.derive_geometry(cfg)
+    ell = synth.phantom_for(cfg, g, synth.phantom_seed(1))
+    sino = synth.add_noise(synth.project(g, ell), cfg["noise_sigma"], synth.noise_seed(1))
+    return cfg, g, sino.astype(np.float32)
+
+
+def multipitch_case(endpoint_mode=0):
+    """Config-1 scanner with a 150-slice volume: 2.6 pitches, so slices reuse
+    the one-pitch tables with shifted views; ragged 61 x 45 xy grid."""
+    cfg = dict(synth.config(1))
+    cfg.update(nx=61, ny=45, nz=150, turns=5, endpoint_mode=endpoint_mode)
+    g = oracle.derive_geometry(cfg)
+    ell = synth.phantom_for(dict(cfg, phantom="shepp_style"), g, 77)
+    sino = synth.project(g, ell)
+    return cfg, g, sino.astype(np.float32)
+
+
+def odd_case():
+    """Small geometry exercising every offset and parity: odd sizes, non-zero
+    lambda0 / z0 / lambda_first / alpha and w offsets, odd n_psi, an axis voxel."""
+    cfg = dict(R=300.0, D=620.0, views_per_turn=90, turns=4, n_rows=13, n_cols=53, n_cols_full=53, col_keep=1,
+               det_half_width=21.0, nx=21, ny=17, nz=23, voxel=1.5, pitch_factor=1.0, n_psi=31)
+    g = oracle.derive_geometry(cfg)
+    g.update(lambda0=0.7, z0=-4.0, lambda_first=0.11, alpha_offset=0.25 * g["d_alpha"], w_offset=0.3 * g["d_w"])
+    # re-centre the volume in the (shifted) scan, keep z_first on the slice grid
+    dl = 2 * math.pi / g["views_per_turn"]
+    h = g["P"] / (2 * math.pi)
+    zc = g["z0"] + h * (g["lambda_first"] + 0.5 * g["n_views"] * dl)
+    g["z_first"] = zc - 0.5 * (g["nz"] - 1) * g["dz"]
+    rng = np.random.default_rng(5)
+    sino = rng.normal(size=(g["n_views"], g["n_rows"], g["n_cols"]))
+    return cfg, g, sino.astype(np.float32)
+
+
+def near_tie(frac, tol=1e-9):
+    f = np.asarray(frac, dtype=np.float64)
+    return (f < tol) | (f > 1 - tol)

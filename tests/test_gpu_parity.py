@@ -1,0 +1,183 @@
+"""GPU path vs the FP64 oracle, through the C ABI (via the ctypes binding).
+
+Bars: integer tables bit-exact (a mismatch is allowed only where the oracle's
+fractional part is within 1e-9 of an integer, i.e. a floor tie between two
+correctly rounded FP64 evaluations); FP32 results within rel-L2 1e-5 of the
+oracle on the same FP32-rounded input.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from cases import c1_case, multipitch_case, near_tie, odd_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+@pytest.fixture(scope="module")
+def kats():
+    from paper_2201_02309_b300 import build
+    build.build()
+    import paper_2201_02309_b300 as k
+    return k
+
+
+def check_int_table(got, want, want_frac, name):
+    bad = got != want
+    if bad.any():
+        ties = near_tie(want_frac)
+        assert not (bad & ~ties).any(), f"{name}: {int((bad & ~ties).sum())} mismatches away from ties"
+    return int(bad.sum())
+
+
+def compare_tables(kp, op):
+    assert check_int_table(kp.table("kappa_idx"), op.kap[0], op.kap[1], "kappa") <= 2
+    same = kp.table("kappa_idx") == op.kap[0]
+    assert np.abs(kp.table("kappa_frac") - op.kap[1])[same].max() < 2e-7
+    assert check_int_table(kp.table("psi_idx"), op.psi[0], op.psi[1], "psi") <= 2
+    same = kp.table("psi_idx") == op.psi[0]
+    assert np.abs(kp.table("psi_frac") - op.psi[1])[same].max() < 2e-7
+    if op.pi is not None:
+        for a, b in (("k0", "w0"), ("k1", "w1")):
+            n = check_int_table(kp.table(a), op.pi[a], op.pi[b], a)
+            assert n <= 2
+            same = kp.table(a) == op.pi[a]
+            assert np.abs(kp.table(b) - op.pi[b])[same].max() < 2e-7
+
+
+@pytest.fixture(scope="module")
+def c1(kats):
+    cfg, g, sino = c1_case()
+    return g, sino, oracle.Plan(g), kats.Plan(g)
+
+
+def test_tables_c1(c1):
+    g, _, op, kp = c1
+    compare_tables(kp, op)
+
+
+def test_plan_info_c1(c1):
+    g, _, op, kp = c1
+    info = kp.info
+    N = oracle.pitch_slices(g)
+    assert info["slices_per_pitch"] == N
+    assert info["update_count"] == op.update_count()
+    s = np.arange(g["nz"])
+    kmin = min(int(op.pi["k0"][j].min()) + (ss // N) * g["views_per_turn"] for ss, j in zip(s, s % N))
+    kmax = max(int(op.pi["k1"][j].max()) + (ss // N) * g["views_per_turn"] for ss, j in zip(s, s % N))
+    assert info["first_view"] == kmin and info["n_filtered_views"] == kmax - kmin + 1
+    ext = op.extents()
+    assert abs(info["lambda_min"] - ext[0]) < 1e-12 and abs(info["lambda_max"] - ext[1]) < 1e-12
+    assert np.allclose([info["alpha_min"], info["alpha_max"]], ext[2:4], rtol=1e-5, atol=1e-7)
+    assert np.allclose([info["w_min"], info["w_max"]], ext[4:6], rtol=1e-5, atol=1e-5)
+    assert info["alpha_m"] == pytest.approx(oracle.alpha_m(g), rel=1e-15)
+
+
+def test_pi_endpoints_fp64(kats):
+    _, g, _ = odd_case()
+    rng = np.random.default_rng(2)
+    pts = np.stack([rng.uniform(-0.9, 0.9, 400) * 200, rng.uniform(-0.9, 0.9, 400) * 200,
+                    rng.uniform(-300, 300, 400)], 1)
+    pts[0] = (0.0, 0.0, 12.5)
+    li, lo = kats.pi_endpoints(g, pts)
+    want = np.array([oracle.pi_endpoints(g, *p) for p in pts])
+    assert np.abs(li - want[:, 0]).max() < 1e-11
+    assert np.abs(lo - want[:, 1]).max() < 1e-11
+
+
+def test_filter_parity_c1(c1, torch):
+    g, sino, op, kp = c1
+    gF = kp.filter(torch.from_numpy(sino).cuda()).cpu().numpy()
+    v0, nv = kp.info["first_view"], kp.info["n_filtered_views"]
+    want = op.filter(sino.astype(np.float64), v0, nv)
+    assert rel_l2(gF, want) < TOL
+
+
+def test_backproject_parity_c1(c1, torch):
+    g, sino, op, kp = c1
+    v0, nv = kp.info["first_view"], kp.info["n_filtered_views"]
+    gF = op.filter(sino.astype(np.float64), v0, nv).astype(np.float32)
+    vol = kp.backproject(torch.from_numpy(gF).cuda()).cpu().numpy()
+    want = op.backproject(gF.astype(np.float64), v0)
+    assert rel_l2(vol, want) < TOL
+
+
+def test_recon_parity_c1(c1, torch):
+    g, sino, op, kp = c1
+    vol = kp.recon(torch.from_numpy(sino).cuda()).cpu().numpy()
+    want = op.recon(sino.astype(np.float64))
+    assert rel_l2(vol, want) < TOL
+
+
+def test_adjoint_parity_c1(c1, torch):
+    g, _, op, kp = c1
+    rng = np.random.default_rng(9)
+    y = rng.normal(size=kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    want = op.adjoint(y.astype(np.float64))
+    assert rel_l2(got, want) < TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_multipitch_ragged(kats, torch, mode):
+    _, g, sino = multipitch_case(mode)
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    compare_tables(kp, op)
+    assert kp.info["update_count"] == op.update_count()
+    vol = kp.recon(torch.from_numpy(sino).cuda()).cpu().numpy()
+    assert rel_l2(vol, op.recon(sino.astype(np.float64))) < TOL
+    y = np.random.default_rng(1).normal(size=kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel_l2(got, op.adjoint(y.astype(np.float64))) < TOL
+
+
+def test_odd_geometry_batch(kats, torch):
+    _, g, sino = odd_case()
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    compare_tables(kp, op)
+    batch = np.stack([sino, -0.5 * sino + 0.1])
+    vol = kp.recon(torch.from_numpy(batch).cuda()).cpu().numpy()
+    for b in range(2):
+        assert rel_l2(vol[b], op.recon(batch[b].astype(np.float64))) < TOL
+    y = np.random.default_rng(3).normal(size=(2,) + kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    for b in range(2):
+        assert rel_l2(got[b], op.adjoint(y[b].astype(np.float64))) < TOL
+
+
+def test_recon_host_matches_device(c1, torch):
+    g, sino, op, kp = c1
+    dev = kp.recon(torch.from_numpy(sino).cuda()).cpu()
+    hs = torch.from_numpy(sino).pin_memory()
+    hv = torch.empty(kp.vol_shape, dtype=torch.float32).pin_memory()
+    kp.recon_host(hs, hv)
+    assert torch.equal(dev, hv)
+
+
+def test_errors(c1, torch, kats):
+    g, sino, op, kp = c1
+    x = torch.from_numpy(sino).cuda()
+    out = torch.empty(kp.vol_shape, device="cuda")
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(kats.KatsevichError) as e:
+        kp.recon(x, out=out, workspace=small)
+    assert e.value.status == kats.native.KATS_ESPACE
+    with pytest.raises(kats.KatsevichError) as e:
+        kats.native.katsevich_recon(kp.handle, x.data_ptr(), out.data_ptr(), 0, 0, small.data_ptr(), 16, 0)
+    assert e.value.status == kats.native.KATS_EINVAL
+    with pytest.raises(ValueError):
+        kp.recon(x[:-1].contiguous())
+    # a volume whose PI windows leave the scan is rejected at plan time
+    g2 = dict(g)
+    g2["z_first"] = g["z_first"] + 4 * g["P"]
+    with pytest.raises(kats.KatsevichError) as e:
+        kats.Plan(g2)
+    assert e.value.status == kats.native.KATS_EGEOM
