@@ -41,7 +41,21 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
+    ap.add_argument("--turns", type=int, default=None, help="fewer helix turns (profiling captures only)")
     return ap.parse_args()
+
+
+def config_for(args):
+    import synth
+    cfg = synth.config(args.config)
+    if args.nz:
+        cfg["nz"] = args.nz
+        cfg["name"] += f"_nz{args.nz}"
+    if args.turns:
+        cfg["turns"] = args.turns
+        cfg["name"] += f"_turns{args.turns}"
+    return cfg
 
 
 def peaks():
@@ -99,11 +113,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def workload(cfg_index, geom):
+def workload(cfg_index, geom, cfg):
     import numpy as np
 
     import synth
-    cfg = synth.config(cfg_index)
     ell = synth.phantom_for(cfg, geom, synth.phantom_seed(cfg_index))
     sino = synth.project(geom, ell)
     sino = synth.add_noise(sino, cfg["noise_sigma"], synth.noise_seed(cfg_index))
@@ -161,7 +174,7 @@ def run_reference(args):
         return
     import oracle
     import synth
-    cfg = synth.config(args.config)
+    cfg = config_for(args)
     g = oracle.derive_geometry(cfg)
     # the oracle's own one-pitch table gives the update count and the filtered view window
     t = oracle.pi_table(g)
@@ -172,7 +185,7 @@ def run_reference(args):
     kmax = max(int(t["k1"][x % N].max()) + (x // N) * g["views_per_turn"] for x in s)
     info = {"first_view": kmin, "n_filtered_views": kmax - kmin + 1, "update_count": upd,
             "slices_per_pitch": N, "n_psi": oracle.n_psi(g), "workspace_bytes": 0}
-    _, sino = workload(args.config, g)
+    _, sino = workload(args.config, g, cfg)
     vals = []
     for i in range(args.warmup + args.steps):
         r = oracle_sample(g, sino, info, n_views=16, n_vox=8192, seed=i)
@@ -209,9 +222,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    cfg = synth.config(args.config)
+    cfg = config_for(args)
     g = kats.make_geometry(cfg)
-    cfg, sino_np = workload(args.config, g)
+    cfg, sino_np = workload(args.config, g, cfg)
     plan = kats.Plan(g)
     info = plan.info
     sino = torch.from_numpy(sino_np).to(dev)
