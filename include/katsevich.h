@@ -201,6 +201,30 @@ KATS_API int katsevich_plan_table(const kats_plan *plan, int which, void *host_d
 KATS_API int katsevich_pi_endpoints(const kats_geometry *g, int64_t n, const double *host_xyz,
                            double *host_lam_i, double *host_lam_o);
 
+/*
+ * katsevich_recon without a caller workspace, for callers that cannot
+ * allocate device memory when they reconstruct: services whose device memory
+ * is reserved up front by another allocator, or loops where a cudaMalloc /
+ * cudaFree (which may synchronise the device) would stall other streams.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * Same operator, layouts and FP32 precision as katsevich_recon.  The scratch
+ * is a fixed array of KATS_NOALLOC_SCRATCH_BYTES in the library's device
+ * memory (every GPU that loads the library holds one copy until the process
+ * exits).  Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ * call.  Geometries whose scratch (filtered views plus filter intermediates)
+ * exceeds the array are rejected with KATS_ESPACE and a message giving both
+ * sizes; use katsevich_recon for them.  The first call on a device looks up
+ * the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different threads) race and corrupt each other's results: serialise them.
+ * Every scratch element read is written earlier by the same call, so no
+ * state carries over from the previous call.
+ */
+#define KATS_NOALLOC_SCRATCH_BYTES (64u << 20)
+KATS_API int katsevich_recon_noalloc(const kats_plan *plan, const float *sino, float *vol, int batch, void *stream);
+
 /* Release a plan's device memory.  NULL is allowed. */
 KATS_API void katsevich_plan_destroy(kats_plan *plan);
 

@@ -19,7 +19,8 @@ _STATUS = {1: "KATS_EINVAL", 2: "KATS_EGEOM", 3: "KATS_ENOMEM", 4: "KATS_ECUDA",
 EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "katsevich_workspace_bytes",
            "katsevich_recon", "katsevich_adjoint", "katsevich_filter", "katsevich_backproject",
            "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
-           "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error"]
+           "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error",
+           "katsevich_recon_noalloc"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -80,6 +81,7 @@ def load() -> ctypes.CDLL:
         "katsevich_plan_table": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_size_t]),
         "katsevich_pi_endpoints": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_int64, P, P, P]),
         "katsevich_plan_destroy": (None, [P]),
+        "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -164,6 +166,10 @@ def katsevich_plan_table(plan, which, dst_ptr, nbytes) -> None:
 def katsevich_pi_endpoints(geom: dict, n, xyz_ptr, li_ptr, lo_ptr) -> None:
     g = geometry_struct(geom)
     check(load().katsevich_pi_endpoints(ctypes.byref(g), n, xyz_ptr, li_ptr, lo_ptr))
+
+
+def katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr) -> None:
+    check(load().katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr))
 
 
 def katsevich_plan_destroy(plan) -> None:
