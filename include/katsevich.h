@@ -103,6 +103,7 @@ typedef struct kats_plan_info {
     int64_t first_view;       /* first filtered half-view the volume needs             */
     int64_t n_filtered_views; /* filtered half-views needed (sinogram views: +1)       */
     int64_t update_count;     /* sum over voxels of their PI-window view counts        */
+    int64_t gf_cols;          /* row pitch of filtered data: n_cols rounded up to 4    */
     int64_t workspace_bytes;  /* per concurrent call, FP32 storage                     */
     int64_t plan_bytes;       /* device bytes held by the plan                         */
 } kats_plan_info;
@@ -163,15 +164,17 @@ KATS_API int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, flo
 
 /*
  * Steps 1-6 only (Sec. II Eqs. (Deriv), (LW), (FR), (HF), (BR), (PW)):
- * sino [batch][n_views][n_rows][n_cols] -> gF [batch][n_filtered_views][n_rows][n_cols],
- * filtered view v of the output is half-view first_view + v.
+ * sino [batch][n_views][n_rows][n_cols] -> gF [batch][n_filtered_views][n_rows][gf_cols]
+ * (rows padded to gf_cols = n_cols rounded up to 4 floats, pad columns written
+ * as 0); filtered view v of the output is half-view first_view + v.
  */
 KATS_API int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int batch,
                      int precision, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
- * Step 7 only (Sec. II backprojection step): gF [batch][n_filtered_views][n_rows][n_cols]
- * (layout of katsevich_filter's output, FP32) -> vol [batch][nz][ny][nx].
+ * Step 7 only (Sec. II backprojection step): gF [batch][n_filtered_views][n_rows][gf_cols]
+ * (layout of katsevich_filter's output, FP32, 16-byte aligned, pad columns 0)
+ * -> vol [batch][nz][ny][nx].
  */
 KATS_API int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, int batch, void *stream);
 
@@ -224,6 +227,14 @@ KATS_API int katsevich_pi_endpoints(const kats_geometry *g, int64_t n, const dou
  */
 #define KATS_NOALLOC_SCRATCH_BYTES (64u << 20)
 KATS_API int katsevich_recon_noalloc(const kats_plan *plan, const float *sino, float *vol, int batch, void *stream);
+
+/*
+ * Device status of a plan's kernels: waits inside the kernels are bounded;
+ * one that gives up records KATS_ETIMEOUT-class status here instead of
+ * hanging.  Synchronises the device, returns the word in *status (0 = ok) and
+ * clears it.
+ */
+KATS_API int katsevich_device_status(const kats_plan *plan, int *status);
 
 /* Release a plan's device memory.  NULL is allowed. */
 KATS_API void katsevich_plan_destroy(kats_plan *plan);

@@ -100,8 +100,9 @@ class Plan:
 
     @property
     def filtered_shape(self):
+        """[views][rows][gf_cols]: rows padded to a multiple of 4 floats, pad columns zero."""
         g = self.geom
-        return (self.info["n_filtered_views"], g["n_rows"], g["n_cols"])
+        return (self.info["n_filtered_views"], g["n_rows"], self.info["gf_cols"])
 
     def workspace(self, precision=KATS_PREC_FP32, device=None):
         """A cached device workspace (torch uint8) big enough for recon/adjoint."""

@@ -8,7 +8,8 @@ using namespace kats;
 
 namespace {
 
-size_t gf_bytes(const Plan &p) { return sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.g.n_cols); }
+size_t gf_bytes(const Plan &p) { return sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols); }
+size_t gf_item(const Plan &p) { return (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols); }
 size_t sino_item(const Plan &p) { return (size_t)(p.g.n_views * p.g.n_rows * p.g.n_cols); }
 size_t vol_item(const Plan &p) { return (size_t)(p.g.nx * p.g.ny * p.g.nz); }
 size_t view_elems(const Plan &p) { return (size_t)(p.g.n_rows * p.g.n_cols); }
@@ -70,8 +71,8 @@ int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int ba
     }
     cudaStream_t st = (cudaStream_t)stream;
     for (int b = 0; b < batch; ++b) {
-        rc = launch_filter(p, sino + b * sino_item(p) + p.first_view * view_elems(p), gF + b * p.n_fviews * view_elems(p),
-                           workspace, workspace_bytes, st);
+        rc = launch_filter(p, sino + b * sino_item(p) + p.first_view * view_elems(p), gF + b * gf_item(p), workspace,
+                           workspace_bytes, st);
         if (rc) return rc;
     }
     return KATS_OK;
@@ -86,7 +87,7 @@ int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, in
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
     cudaStream_t st = (cudaStream_t)stream;
     for (int b = 0; b < batch; ++b) {
-        int rc = launch_backproject(p, gF + b * p.n_fviews * view_elems(p), vol + b * vol_item(p), st);
+        int rc = launch_backproject(p, gF + b * gf_item(p), vol + b * vol_item(p), st);
         if (rc) return rc;
     }
     return KATS_OK;

@@ -4,11 +4,23 @@
 // with the one-pitch PI table reused for every pitch (Sec. II periodicity:
 // slice s reads table slice s mod N and shifts its views by (s div N) turns).
 //
-// Thread mapping: one thread owns one (x, y) column and BP_T consecutive
-// slices held in registers.  alpha* and v* do not depend on z and w* is affine
-// in z, so the per-view geometry (trig, atan, rsqrt) is computed once per view
-// and reused by the thread's BP_T slices.
+// Thread mapping (both kernels): one thread owns one (x, y) column and T
+// consecutive slices held in registers.  alpha* and v* do not depend on z and
+// w* is affine in z, so the per-view geometry (trig, atan, rsqrt) is computed
+// once per view and reused by the thread's T slices.
+//
+// k_backproject_tma (main path): a CTA owns a 16 x 16 column tile and 8
+// slices.  For each view a producer warp copies its detector window (all rows
+// plus zero rows above and below, a column range covering the tile's
+// projection) into a ring of shared-memory slots by TMA; eight consumer warps
+// read every bilinear tap as a plain shared-memory load with no bounds test.
+// k_backproject (fallback for windows TMA cannot stage): the same arithmetic
+// with bounds-tested loads from global memory.
+#include <cuda.h>
+
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -18,12 +30,12 @@ constexpr int BP_T = 8;  // slices per thread
 constexpr int BP_BX = 16, BP_BY = 8;
 
 struct BPArgs {
-    const float *gF;  // [n_fviews][n_rows][n_cols], view 0 = half-view first_view
+    const float *gF;  // [n_fviews][n_rows][gcols], view 0 = half-view first_view
     float *vol;       // [nz][ny][nx]
     const int32_t *k0, *k1;
     const float *w0, *w1;
     const float2 *trig;
-    int nx, ny, nz, N, vpt, n_rows, n_cols;
+    int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
     int64_t first_view;
     float R, D, x0, y0, dx, dy;
     float alpha0, inv_da, w0row, inv_dw, dz_over_dw, scale;
@@ -31,11 +43,12 @@ struct BPArgs {
     double z_first, dz, z0, h, lambda_first, dlam;
 };
 
-__device__ __forceinline__ float tap(const float *view, int r, int c, int n_rows, int n_cols)
+__device__ __forceinline__ float tap(const float *view, int r, int c, int n_rows, int n_cols, int gcols)
 {
-    return (r >= 0 && r < n_rows && c >= 0 && c < n_cols) ? __ldg(view + r * n_cols + c) : 0.0f;
+    return (r >= 0 && r < n_rows && c >= 0 && c < n_cols) ? __ldg(view + r * gcols + c) : 0.0f;
 }
 
+// ------------------------------------------------------------ fallback kernel
 __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 {
     const int ix = blockIdx.x * BP_BX + threadIdx.x;
@@ -69,7 +82,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kmin + 0.5) * a.dlam));
     const float hdl = (float)(a.h * a.dlam);
     int km = ((kmin % a.vpt) + a.vpt) % a.vpt;
-    const int64_t per_view = (int64_t)a.n_rows * a.n_cols;
+    const int64_t per_view = (int64_t)a.n_rows * a.gcols;
     for (int k = kmin; k <= kmax; ++k) {
         const float2 cs = __ldg(a.trig + km);
         km = (km + 1 == a.vpt) ? 0 : km + 1;
@@ -94,10 +107,10 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
             const float rf = floorf(ur);
             const int ri = (int)rf;
             const float fr = ur - rf;
-            const float v00 = tap(view, ri, ci, a.n_rows, a.n_cols);
-            const float v01 = tap(view, ri, ci + 1, a.n_rows, a.n_cols);
-            const float v10 = tap(view, ri + 1, ci, a.n_rows, a.n_cols);
-            const float v11 = tap(view, ri + 1, ci + 1, a.n_rows, a.n_cols);
+            const float v00 = tap(view, ri, ci, a.n_rows, a.n_cols, a.gcols);
+            const float v01 = tap(view, ri, ci + 1, a.n_rows, a.n_cols, a.gcols);
+            const float v10 = tap(view, ri + 1, ci, a.n_rows, a.n_cols, a.gcols);
+            const float v11 = tap(view, ri + 1, ci + 1, a.n_rows, a.n_cols, a.gcols);
             const float top = v00 + fc * (v01 - v00);
             const float bot = v10 + fc * (v11 - v10);
             acc[t] = fmaf(om * inv_v, top + fr * (bot - top), acc[t]);
@@ -110,6 +123,273 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     }
 }
 
+// ---------------------------------------------------------------- TMA kernel
+// CTA = B2_TX x B2_TY columns x B2_T slices: B2_CW consumer warps (one thread
+// per column) plus one producer warp that stages each view's detector window
+// into a ring of B2_R shared-memory slots (full/empty mbarrier pairs).
+constexpr int B2_TX = 16, B2_TY = 16, B2_T = 8, B2_R = 5;
+constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
+constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
+constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
+
+struct BP2Args {
+    BPArgs a;
+    int W;            // staged columns per view (multiple of 4)
+    int srows;        // staged rows: n_rows + 3 (row 0 and rows n_rows+1.. are zero fill)
+    int slot_floats;  // floats per staged view, multiple of 32 (128-byte slots)
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Column of the detector grid where alpha*(lambda, x, y) falls, in FP32.
+__device__ __forceinline__ float column_of(const BPArgs &a, float2 cs, float x, float y)
+{
+    const float v = a.R - x * cs.x - y * cs.y;
+    const float u = -x * cs.y + y * cs.x;
+    return (atanf(u * (1.0f / v)) - a.alpha0) * a.inv_da;
+}
+
+// One view's contribution to a thread's B2_T slices.  WEIGHTED: views at the
+// ends of some slice's PI window (fractional or zero weights); otherwise every
+// slice takes the view with weight 1.
+template <bool WEIGHTED>
+__device__ __forceinline__ void bp_view(const float *col, int W, float fc, float ur0, float dur, float rmax,
+                                        float inv_v, float kf, const float *lo, const float *hi, float *acc)
+{
+#pragma unroll
+    for (int t = 0; t < B2_T; ++t) {
+        const float ur = fminf(fmaxf(fmaf((float)t, dur, ur0), 0.0f), rmax);
+        const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur)
+        const int ri = __float_as_int(yv) - 0x4B000000;
+        const float fr = ur - (yv - 8388608.0f);
+        const float *q = col + ri * W;
+        const float v00 = q[0], v01 = q[1], v10 = q[W], v11 = q[W + 1];
+        const float top = fmaf(fc, v01 - v00, v00);
+        const float bot = fmaf(fc, v11 - v10, v10);
+        const float val = fmaf(fr, bot - top, top);
+        if (WEIGHTED) {
+            const float om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
+            acc[t] = fmaf(om * inv_v, val, acc[t]);
+        } else {
+            acc[t] = fmaf(inv_v, val, acc[t]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(B2_THREADS, 2)
+    k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
+{
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    // [B2_R][slot_floats], base rounded up to 128 bytes (TMA destinations)
+    float *const s_views = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(s_raw) + 127) & ~(uintptr_t)127);
+    __shared__ __align__(8) uint64_t s_full[B2_R], s_empty[B2_R];
+    __shared__ int s_col[B2_R];
+    __shared__ int s_K0, s_K1, s_abort;
+    const BPArgs &a = p.a;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool producer = warp == B2_CW;
+    const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
+    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    const int s0 = blockIdx.z * B2_T;
+    const bool active = !producer && ix < a.nx && iy < a.ny;
+
+    // per-slice view windows; weights omega(k) = sat(k - lo_t) * sat(hi_t - k) relative to kbase
+    int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
+    float lo[B2_T], hi[B2_T], acc[B2_T];
+    {
+        int ka[B2_T], kb[B2_T];
+        float wa[B2_T], wb[B2_T];
+#pragma unroll
+        for (int t = 0; t < B2_T; ++t) {
+            const int s = s0 + t;
+            ka[t] = INT32_MAX;
+            kb[t] = INT32_MIN;
+            wa[t] = wb[t] = 0.0f;
+            if (active && s < a.nz) {
+                const int j = s % a.N, m = s / a.N;
+                const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
+                ka[t] = a.k0[o] + m * a.vpt;
+                kb[t] = a.k1[o] + m * a.vpt;
+                wa[t] = a.w0[o];
+                wb[t] = a.w1[o];
+                kmin = min(kmin, ka[t]);
+                kmax = max(kmax, kb[t]);
+            }
+            kfull_lo = max(kfull_lo, ka[t]);
+            kfull_hi = min(kfull_hi, kb[t]);
+        }
+        const int kbase = active ? kmin : 0;
+#pragma unroll
+        for (int t = 0; t < B2_T; ++t) {
+            acc[t] = 0.0f;
+            if (ka[t] <= kb[t]) {
+                lo[t] = (float)(ka[t] - kbase) - wa[t];
+                hi[t] = (float)(kb[t] - kbase) + wb[t];
+            } else {
+                lo[t] = 3.0e9f;
+                hi[t] = -3.0e9f;
+            }
+        }
+    }
+
+    if (tid == 0) {
+        s_K0 = INT32_MAX;
+        s_K1 = INT32_MIN;
+        s_abort = 0;
+        for (int r = 0; r < B2_R; ++r) {
+            mbar_init(&s_full[r], 1);
+            mbar_init(&s_empty[r], B2_CW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (active) {
+        atomicMin(&s_K0, kmin);
+        atomicMax(&s_K1, kmax);
+    }
+    __syncthreads();
+    const int K0 = s_K0, K1 = s_K1;
+    if (K0 > K1) return;  // no active voxel in this CTA (uniform exit)
+    const int nviews = K1 - K0 + 1;
+
+    if (producer) {
+        // ---------------- producer warp: column window + TMA for each view
+        const int ixa = blockIdx.x * B2_TX, iya = blockIdx.y * B2_TY;
+        // tile corners (voxel centres inside the volume): alpha* over the tile
+        // is extremal at them (u*/v* is linear-fractional in (x, y))
+        const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
+        const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
+        const uint32_t box_bytes = (uint32_t)(p.W * p.srows * 4);
+        int issued = 0;
+        for (int j = 0; j < nviews; ++j) {
+            const int slot = j % B2_R, use = j / B2_R;
+            if (use > 0 && !mbar_wait(&s_empty[slot], (uint32_t)((use - 1) & 1))) {
+                if (lane == 0) atomicOr(&s_abort, 1);
+                break;
+            }
+            if (*((volatile int *)&s_abort)) break;
+            const int k = K0 + j;
+            const int kmod = ((k % a.vpt) + a.vpt) % a.vpt;
+            float c = column_of(a, __ldg(a.trig + kmod), cx, cy);
+            c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
+            c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
+            if (lane == 0) {
+                // one column of slack left of the lowest tap, start aligned to 4 floats (16 bytes)
+                const int clo = ((int)floorf(c) - 1) & ~3;
+                s_col[slot] = clo;
+                mbar_arrive_expect_tx(&s_full[slot], box_bytes);
+                tma_load_3d(s_views + (size_t)slot * p.slot_floats, &gmap, &s_full[slot], clo, -1,
+                            k - (int)a.first_view);
+            }
+            __syncwarp();
+            issued = j + 1;
+        }
+        if (lane == 0 && *((volatile int *)&s_abort)) {
+            // let every issued copy land before the CTA's shared memory is released
+            for (int j = max(0, issued - B2_R); j < issued; ++j)
+                mbar_wait(&s_full[j % B2_R], (uint32_t)((j / B2_R) & 1));
+            atomicExch(p.status, kDevStatusTimeout);
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
+    const int kbase = active ? kmin : 0;
+    const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 -
+                             a.h * (a.lambda_first + ((double)kbase + 0.5) * a.dlam));
+    const float hdl = (float)(a.h * a.dlam);
+    const float rmax = (float)(a.n_rows + 1);
+    int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;  // view index mod views_per_turn
+    for (int j = 0; j < nviews; ++j) {
+        const int slot = j % B2_R;
+        const int k = K0 + j;
+        const int km = kmod;
+        kmod = (kmod + 1 == a.vpt) ? 0 : kmod + 1;
+        if (!mbar_wait(&s_full[slot], (uint32_t)((j / B2_R) & 1))) {
+            if (lane == 0) atomicOr(&s_abort, 1);
+            break;
+        }
+        if (active && k >= kmin && k <= kmax) {
+            const float *sl = s_views + (size_t)slot * p.slot_floats;
+            const float2 cs = __ldg(a.trig + km);
+            const float v = a.R - x * cs.x - y * cs.y;
+            const float u = -x * cs.y + y * cs.x;
+            const float inv_v = 1.0f / v;
+            const float uc = (atanf(u * inv_v) - a.alpha0) * a.inv_da - (float)s_col[slot];
+            const float cf = floorf(uc);
+            const float fc = uc - cf;
+            const int ci = min(max((int)cf, 0), p.W - 2);
+            const float M = a.D * rsqrtf(u * u + v * v);  // D cos(alpha*) / v*
+            const float kf = (float)(k - kbase);
+            const float ur0 = (M * (zb - hdl * kf) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
+            const float dur = M * a.dz_over_dw;
+            if (k > kfull_lo && k < kfull_hi)
+                bp_view<false>(sl + ci, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+            else
+                bp_view<true>(sl + ci, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[slot]);
+        if (*((volatile int *)&s_abort)) break;
+    }
+    if (!active || *((volatile int *)&s_abort)) return;
+#pragma unroll
+    for (int t = 0; t < B2_T; ++t) {
+        const int s = s0 + t;
+        if (s < a.nz) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = acc[t] * a.scale;
+    }
+}
+
+// ----------------------------------------------------------------- launch
 static BPArgs bp_args(const Plan &p)
 {
     const kats_geometry &g = p.g;
@@ -126,6 +406,7 @@ static BPArgs bp_args(const Plan &p)
     a.vpt = (int)g.views_per_turn;
     a.n_rows = (int)g.n_rows;
     a.n_cols = (int)g.n_cols;
+    a.gcols = (int)p.gf_cols;
     a.first_view = p.first_view;
     a.R = (float)g.R;
     a.D = (float)g.D;
@@ -148,11 +429,70 @@ static BPArgs bp_args(const Plan &p)
     return a;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+    });
+    return fn;
+}
+
+// Staged window width: the tile's columns (B2_TX x B2_TY voxel centres) subtend at
+// most 2 atan(L / 2 d) with L the tile diagonal and d = R - r_fov the nearest
+// source distance; add floor and alignment slack.
+static int window_cols(const Plan &p)
+{
+    const kats_geometry &g = p.g;
+    const double L = std::hypot((B2_TX - 1) * g.dx, (B2_TY - 1) * g.dy);
+    const double xa = fabs(g.x0 - 0.5 * g.dx), xb = fabs(g.x0 + ((double)g.nx - 0.5) * g.dx);
+    const double ya = fabs(g.y0 - 0.5 * g.dy), yb = fabs(g.y0 + ((double)g.ny - 0.5) * g.dy);
+    const double rf = std::hypot(std::max(xa, xb), std::max(ya, yb));
+    const double span = 2.0 * atan(L / (2.0 * (g.R - rf))) / g.d_alpha;
+    return ((int)ceil(span) + 8 + 3) / 4 * 4;
+}
+
 int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st)
 {
     BPArgs a = bp_args(p);
     a.gF = gF;
     a.vol = vol;
+    const int W = window_cols(p);
+    const int srows = (int)p.g.n_rows + 3;
+    const int slot = (W * srows + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * (size_t)slot * B2_R + 128;  // + base alignment slack
+    EncodeTiledFn enc = encode_fn();
+    const bool tma_ok = enc && W <= 256 && W <= p.gf_cols && srows <= 256 && smem <= 200 * 1024 &&
+                        (reinterpret_cast<uintptr_t>(gF) % 16) == 0 && p.n_fviews < INT32_MAX;
+    if (tma_ok) {
+        CUtensorMap map;
+        cuuint64_t dims[3] = {(cuuint64_t)p.gf_cols, (cuuint64_t)p.g.n_rows, (cuuint64_t)p.n_fviews};
+        cuuint64_t strides[2] = {(cuuint64_t)p.gf_cols * 4, (cuuint64_t)(p.gf_cols * p.g.n_rows) * 4};
+        cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)srows, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)gF, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS) {
+            BP2Args b{a, W, srows, slot, p.dev_status};
+            KATS_CUDA(cudaFuncSetAttribute(k_backproject_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
+                      (unsigned)ceil_div(p.g.nz, B2_T));
+            k_backproject_tma<<<grid, B2_THREADS, smem, st>>>(map, b);
+            KATS_CUDA(cudaGetLastError());
+            return KATS_OK;
+        }
+    }
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
     k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);
     KATS_CUDA(cudaGetLastError());
@@ -161,9 +501,9 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
 
 // Transpose of step 7: each (voxel, view) term sends its weight times the
 // voxel value to the four bilinear taps of that view (FP32 atomics).
-__device__ __forceinline__ void splat(float *view, int r, int c, int n_rows, int n_cols, float val)
+__device__ __forceinline__ void splat(float *view, int r, int c, int n_rows, int n_cols, int gcols, float val)
 {
-    if (r >= 0 && r < n_rows && c >= 0 && c < n_cols) atomicAdd(view + r * n_cols + c, val);
+    if (r >= 0 && r < n_rows && c >= 0 && c < n_cols) atomicAdd(view + r * gcols + c, val);
 }
 
 __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const float *__restrict__ vol, float *gF)
@@ -198,7 +538,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
     const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kmin + 0.5) * a.dlam));
     const float hdl = (float)(a.h * a.dlam);
     int km = ((kmin % a.vpt) + a.vpt) % a.vpt;
-    const int64_t per_view = (int64_t)a.n_rows * a.n_cols;
+    const int64_t per_view = (int64_t)a.n_rows * a.gcols;
     for (int k = kmin; k <= kmax; ++k) {
         const float2 cs = __ldg(a.trig + km);
         km = (km + 1 == a.vpt) ? 0 : km + 1;
@@ -224,10 +564,10 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
             const int ri = (int)rf;
             const float fr = ur - rf;
             const float wv = om * inv_v * f[t];
-            splat(view, ri, ci, a.n_rows, a.n_cols, wv * (1.0f - fr) * (1.0f - fc));
-            splat(view, ri, ci + 1, a.n_rows, a.n_cols, wv * (1.0f - fr) * fc);
-            splat(view, ri + 1, ci, a.n_rows, a.n_cols, wv * fr * (1.0f - fc));
-            splat(view, ri + 1, ci + 1, a.n_rows, a.n_cols, wv * fr * fc);
+            splat(view, ri, ci, a.n_rows, a.n_cols, a.gcols, wv * (1.0f - fr) * (1.0f - fc));
+            splat(view, ri, ci + 1, a.n_rows, a.n_cols, a.gcols, wv * (1.0f - fr) * fc);
+            splat(view, ri + 1, ci, a.n_rows, a.n_cols, a.gcols, wv * fr * (1.0f - fc));
+            splat(view, ri + 1, ci + 1, a.n_rows, a.n_cols, a.gcols, wv * fr * fc);
         }
     }
 }
@@ -237,7 +577,7 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
     BPArgs a = bp_args(p);
     a.gF = gF;
     a.vol = nullptr;
-    KATS_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.g.n_cols), st));
+    KATS_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols), st));
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
     k_backproject_T<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a, vol, gF);
     KATS_CUDA(cudaGetLastError());

@@ -23,6 +23,7 @@ struct Plan {
     int64_t nc1;      // half-grid columns (n_cols - 1)
     double alpha_m, psi_max, dpsi, h, dlam;
     int64_t first_view, n_fviews;  // filtered half-views the volume needs
+    int64_t gf_cols;               // row pitch of g^F in floats: n_cols rounded up to 4 (16-byte rows)
     int64_t update_count;
     double ext[6];
     // device tables
@@ -37,8 +38,12 @@ struct Plan {
     float *lw = nullptr;    // [n_rows] length-correction weight
     float *cosa = nullptr;  // [n_cols] cos(alpha_c)
     float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
+    int *dev_status = nullptr;  // device error word (bounded waits that gave up), 0 = ok
     size_t plan_bytes = 0;
 };
+
+// device status codes written to Plan::dev_status
+constexpr int kDevStatusTimeout = 1;
 
 // thread-local error message
 void set_error(const char *fmt, ...);
@@ -55,6 +60,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Kernel launchers (defined in filter.cu, backproject.cu, adjoint.cu).
 // sino points at sinogram view p.first_view; gF receives p.n_fviews filtered views
 int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st);
+// gF: [p.n_fviews][n_rows][p.gf_cols], view 0 = half-view p.first_view, pad columns zero
 int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st);
 int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaStream_t st);
 int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes,

@@ -133,16 +133,22 @@ __global__ void __launch_bounds__(256) k_toeplitz_gemm(const float *__restrict__
 }
 
 // ---------------------------------------------------------------- steps 5-6
+// gF rows have pitch gcols >= n_cols; the pad columns are written as zeros.
 __global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ gF, const int32_t *__restrict__ psi_idx,
                               const float *__restrict__ psi_frac, const float *__restrict__ cosa, int64_t nv,
-                              int n_rows, int n_cols, int n_psi)
+                              int n_rows, int n_cols, int n_psi, int gcols)
 {
-    const int64_t per = (int64_t)n_rows * n_cols;
+    const int64_t per = (int64_t)n_rows * gcols;
     const int64_t total = nv * per;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = t / per;
-        const int rc = (int)(t % per);
-        const int c = rc % n_cols;
+        const int rr = (int)(t % per);
+        const int r = rr / gcols, c = rr % gcols;
+        if (c >= n_cols) {
+            gF[t] = 0.0f;
+            continue;
+        }
+        const int rc = r * n_cols + c;
         const int l = psi_idx[rc];
         const float f = psi_frac[rc];
         const float *col = g4 + v * n_psi * n_cols + c;
@@ -176,9 +182,9 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
     dim3 g2((unsigned)ceil_div(nc, GBN), (unsigned)ceil_div(M, GBM));
     k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, (int)nc, (int)nc, 0);
     KATS_CUDA(cudaGetLastError());
-    const int64_t total = nv * nr * nc;
+    const int64_t total = nv * nr * p.gf_cols;
     k_unrebin_cos<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
-        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np);
+        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
@@ -197,7 +203,7 @@ size_t filter_adjoint_workspace_bytes(const Plan &p)
 // grid (ceil(nc / 32), nv); block 256; smem n_psi * 32 floats.
 __global__ void k_unrebin_cos_T(const float *__restrict__ gF, float *__restrict__ g4a, const int32_t *__restrict__ psi_idx,
                                 const float *__restrict__ psi_frac, const float *__restrict__ cosa, int nv,
-                                int n_rows, int n_cols, int n_psi, int ld4)
+                                int n_rows, int n_cols, int n_psi, int ld4, int gcols)
 {
     extern __shared__ float s[];  // [n_psi][32]
     const int c0 = blockIdx.x * 32, cc = threadIdx.x & 31, c = c0 + cc;
@@ -206,10 +212,10 @@ __global__ void k_unrebin_cos_T(const float *__restrict__ gF, float *__restrict_
     for (int e = threadIdx.x; e < n_psi * 32; e += blockDim.x) s[e] = 0.0f;
     __syncthreads();
     if (c < n_cols) {
-        const float *in = gF + (int64_t)v * n_rows * n_cols;
+        const float *in = gF + (int64_t)v * n_rows * gcols;
         for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) {
             const int rc = r * n_cols + c;
-            const float val = cosa[c] * in[rc];
+            const float val = cosa[c] * in[r * gcols + c];
             const int l = psi_idx[rc];
             const float f = psi_frac[rc];
             if (l >= 0 && l < n_psi) atomicAdd(&s[l * 32 + cc], (1.0f - f) * val);
@@ -293,7 +299,7 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
     if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_unrebin_cos_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     if (sm2 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_rebin_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     k_unrebin_cos_T<<<dim3((unsigned)ceil_div(Kp4, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm1, st>>>(
-        gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp4);
+        gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp4, (int)p.gf_cols);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
     if (ceil_div(M, GBM) > 65535) {

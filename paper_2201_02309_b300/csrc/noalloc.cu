@@ -62,7 +62,7 @@ extern "C" int katsevich_recon_noalloc(const kats_plan *plan, const float *sino,
         set_error("device index %d is above the supported %d", dev, kMaxDevices);
         return KATS_EINVAL;
     }
-    const size_t gf = round256(sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.g.n_cols));
+    const size_t gf = round256(sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols));
     const size_t need = gf + filter_workspace_bytes(p);
     if (need > kScratchBytes) {
         set_error("katsevich_recon_noalloc: this geometry needs %zu bytes of scratch, the static array holds %zu; "

@@ -426,7 +426,7 @@ static void free_plan(Plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
-                    p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig};
+                    p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -456,8 +456,9 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->pi_w0, N * nxy)) || (rc = dalloc(p, &p->pi_w1, N * nxy)) ||
         (rc = dalloc(p, &p->slice_kmin, N)) || (rc = dalloc(p, &p->slice_kmax, N)) ||
         (rc = dalloc(p, &p->hk, 2 * nc - 2)) || (rc = dalloc(p, &p->lw, nr)) || (rc = dalloc(p, &p->cosa, nc)) ||
-        (rc = dalloc(p, &p->trig, g.views_per_turn)))
+        (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->dev_status, 1)))
         return rc;
+    KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
 
     // small 1-D tables in FP64 on the host, stored FP32
     {
@@ -602,7 +603,11 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     if (rc) return rc;
     Plan *p = new Plan();
     p->g = *g;
-    KATS_CUDA(cudaGetDevice(&p->device));
+    cudaError_t de = cudaGetDevice(&p->device);
+    if (de != cudaSuccess) {
+        delete p;
+        return cuda_fail(de, "cudaGetDevice");
+    }
     p->N = N;
     p->n_psi = g->n_psi > 0 ? g->n_psi : 2 * g->n_rows;
     p->nc1 = g->n_cols - 1;
@@ -611,6 +616,7 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->dpsi = 2.0 * p->psi_max / (double)(p->n_psi - 1);
     p->h = g->P / (2.0 * kPi);
     p->dlam = 2.0 * kPi / (double)g->views_per_turn;
+    p->gf_cols = (g->n_cols + 3) / 4 * 4;
     rc = build(p);
     if (rc) {
         free_plan(p);
@@ -640,6 +646,7 @@ int katsevich_plan_info(const kats_plan *plan, kats_plan_info *info)
     info->first_view = p->first_view;
     info->n_filtered_views = p->n_fviews;
     info->update_count = p->update_count;
+    info->gf_cols = p->gf_cols;
     info->workspace_bytes = katsevich_workspace_bytes(plan, KATS_PREC_FP32);
     info->plan_bytes = (int64_t)p->plan_bytes;
     return KATS_OK;
@@ -704,5 +711,18 @@ int katsevich_pi_endpoints(const kats_geometry *g, int64_t n, const double *host
 }
 
 void katsevich_plan_destroy(kats_plan *plan) { free_plan(reinterpret_cast<Plan *>(plan)); }
+
+int katsevich_device_status(const kats_plan *plan, int *status)
+{
+    if (!plan || !status) {
+        set_error("null argument");
+        return KATS_EINVAL;
+    }
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    KATS_CUDA(cudaDeviceSynchronize());
+    KATS_CUDA(cudaMemcpy(status, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*status != 0) KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
+    return KATS_OK;
+}
 
 }  // extern "C"

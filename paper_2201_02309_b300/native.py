@@ -20,7 +20,7 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_recon", "katsevich_adjoint", "katsevich_filter", "katsevich_backproject",
            "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
            "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error",
-           "katsevich_recon_noalloc"]
+           "katsevich_recon_noalloc", "katsevich_device_status"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -43,7 +43,7 @@ class kats_plan_info(ctypes.Structure):
                 ("alpha_m", ctypes.c_double), ("psi_max", ctypes.c_double),
                 ("slices_per_pitch", ctypes.c_int64), ("n_psi", ctypes.c_int64),
                 ("first_view", ctypes.c_int64), ("n_filtered_views", ctypes.c_int64),
-                ("update_count", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("update_count", ctypes.c_int64), ("gf_cols", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_int64)]
 
 
@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
         "katsevich_pi_endpoints": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_int64, P, P, P]),
         "katsevich_plan_destroy": (None, [P]),
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -170,6 +171,12 @@ def katsevich_pi_endpoints(geom: dict, n, xyz_ptr, li_ptr, lo_ptr) -> None:
 
 def katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr) -> None:
     check(load().katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr))
+
+
+def katsevich_device_status(plan) -> int:
+    st = ctypes.c_int()
+    check(load().katsevich_device_status(plan, ctypes.byref(st)))
+    return st.value
 
 
 def katsevich_plan_destroy(plan) -> None:

@@ -53,3 +53,12 @@ def odd_case():
 def near_tie(frac, tol=1e-9):
     f = np.asarray(frac, dtype=np.float64)
     return (f < tol) | (f > 1 - tol)
+
+
+def narrow_case():
+    """Tiny scanner with a 9-column detector (narrower than any staged window)."""
+    cfg = dict(R=100.0, D=200.0, views_per_turn=48, turns=3, n_rows=6, n_cols=9, n_cols_full=9, col_keep=1,
+               det_half_width=4.0, nx=7, ny=5, nz=9, voxel=1.0, pitch_factor=1.0)
+    g = oracle.derive_geometry(cfg)
+    sino = np.random.default_rng(8).normal(size=(g["n_views"], g["n_rows"], g["n_cols"]))
+    return cfg, g, sino.astype(np.float32)

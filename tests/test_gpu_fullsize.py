@@ -57,7 +57,7 @@ def test_c2_filtered_views_sampled(c2):
     v0 = kp.info["first_view"]
     for v in (0, 1777, kp.info["n_filtered_views"] - 1):
         want = op.filter(sino.astype(np.float64), v0 + v, 1)[0]
-        assert rel_l2(gF[v].cpu().numpy(), want) < TOL
+        assert rel_l2(gF[v, :, :g["n_cols"]].cpu().numpy(), want) < TOL
 
 
 def test_c2_voxels_sampled(c2):
@@ -76,3 +76,6 @@ def test_c2_voxels_sampled(c2):
     got = vol[ijk[:, 2], ijk[:, 1], ijk[:, 0]]
     assert rel_l2(got, want) < TOL
     assert np.isfinite(vol).all()
+    assert kp.info["update_count"] > 4.0e10
+    import paper_2201_02309_b300 as kats
+    assert kats.native.katsevich_device_status(kp.handle) == 0

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import c1_case, multipitch_case, near_tie, odd_case, rel_l2
+from cases import c1_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -93,19 +93,27 @@ def test_pi_endpoints_fp64(kats):
     assert np.abs(lo - want[:, 1]).max() < 1e-11
 
 
+def pad_cols(gF, gcols):
+    out = np.zeros(gF.shape[:-1] + (gcols,), np.float32)
+    out[..., :gF.shape[-1]] = gF
+    return out
+
+
 def test_filter_parity_c1(c1, torch):
     g, sino, op, kp = c1
     gF = kp.filter(torch.from_numpy(sino).cuda()).cpu().numpy()
     v0, nv = kp.info["first_view"], kp.info["n_filtered_views"]
     want = op.filter(sino.astype(np.float64), v0, nv)
-    assert rel_l2(gF, want) < TOL
+    assert gF.shape[-1] == kp.info["gf_cols"] and kp.info["gf_cols"] % 4 == 0
+    assert not gF[..., g["n_cols"]:].any()
+    assert rel_l2(gF[..., :g["n_cols"]], want) < TOL
 
 
 def test_backproject_parity_c1(c1, torch):
     g, sino, op, kp = c1
     v0, nv = kp.info["first_view"], kp.info["n_filtered_views"]
     gF = op.filter(sino.astype(np.float64), v0, nv).astype(np.float32)
-    vol = kp.backproject(torch.from_numpy(gF).cuda()).cpu().numpy()
+    vol = kp.backproject(torch.from_numpy(pad_cols(gF, kp.info["gf_cols"])).cuda()).cpu().numpy()
     want = op.backproject(gF.astype(np.float64), v0)
     assert rel_l2(vol, want) < TOL
 
@@ -151,6 +159,23 @@ def test_odd_geometry_batch(kats, torch):
     got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     for b in range(2):
         assert rel_l2(got[b], op.adjoint(y[b].astype(np.float64))) < TOL
+
+
+def test_narrow_detector_fallback_path(kats, torch):
+    # 9-column detector: too narrow for the staged window, so the global-memory kernel runs
+    _, g, sino = narrow_case()
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    compare_tables(kp, op)
+    vol = kp.recon(torch.from_numpy(sino).cuda()).cpu().numpy()
+    assert rel_l2(vol, op.recon(sino.astype(np.float64))) < TOL
+    y = np.random.default_rng(2).normal(size=kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel_l2(got, op.adjoint(y.astype(np.float64))) < TOL
+
+
+def test_device_status_clean(c1, kats):
+    _, _, _, kp = c1
+    assert kats.native.katsevich_device_status(kp.handle) == 0
 
 
 def test_recon_host_matches_device(c1, torch):
