@@ -127,10 +127,18 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 // CTA = B2_TX x B2_TY columns x B2_T slices: B2_CW consumer warps (one thread
 // per column) plus one producer warp that stages each view's detector window
 // into a ring of B2_R shared-memory slots (full/empty mbarrier pairs).
-constexpr int B2_TX = 16, B2_TY = 16, B2_T = 8, B2_R = 5;
+constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16, B2_R = 5;
 constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
 constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
+
+// arctan(t) ~= t * P(t^2) on |t| <= 1: odd minimax polynomial of degree 17
+// fitted by csrc/gen_atan_poly.py (max abs error 5.8e-9 in exact arithmetic,
+// 1.0e-7 with FP32 Horner evaluation, about the error of atanf).
+constexpr int kAtanTerms = 9;
+__constant__ float c_atan[kAtanTerms] = {2.456725342e-03f, -1.440136135e-02f, 3.978122771e-02f,
+                                         -7.234857976e-02f, 1.049894616e-01f, -1.416122913e-01f,
+                                         1.998590678e-01f, -3.333259821e-01f, 9.999998808e-01f};
 
 struct BP2Args {
     BPArgs a;
@@ -179,59 +187,67 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2)
 {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-            "r"(smem_addr(dst)),
+            "r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
         : "memory");
 }
 
-// Column of the detector grid where alpha*(lambda, x, y) falls, in FP32.
-__device__ __forceinline__ float column_of(const BPArgs &a, float2 cs, float x, float y)
+// Detector column coordinate of arctan(t) (t = u*/v*): (atan(t) - alpha0) / d_alpha.
+template <bool POLY>
+__device__ __forceinline__ float column_coord(const BPArgs &a, float t)
 {
-    const float v = a.R - x * cs.x - y * cs.y;
-    const float u = -x * cs.y + y * cs.x;
-    return (atanf(u * (1.0f / v)) - a.alpha0) * a.inv_da;
+    if (POLY) {
+        const float s = t * t;
+        float p = c_atan[0];
+#pragma unroll
+        for (int i = 1; i < kAtanTerms; ++i) p = fmaf(p, s, c_atan[i]);
+        return (t * p - a.alpha0) * a.inv_da;
+    }
+    return (atanf(t) - a.alpha0) * a.inv_da;
 }
 
-// One view's contribution to a thread's B2_T slices.  WEIGHTED: views at the
-// ends of some slice's PI window (fractional or zero weights); otherwise every
-// slice takes the view with weight 1.
-template <bool WEIGHTED>
-__device__ __forceinline__ void bp_view(const float *col, int W, float fc, float ur0, float dur, float rmax,
+// One view's contribution to a thread's B2_T slices, reading taps from
+// smem[col + row * W].  WEIGHTED: the view ends some slice's PI window (end
+// weights, or zero outside it); otherwise every slice takes it with weight 1.
+// CLAMP: keep the row inside the staged window (needed whenever a slice can be
+// outside its PI window or the plan cannot prove rows stay within one row of
+// the detector).
+template <bool WEIGHTED, bool CLAMP>
+__device__ __forceinline__ void bp_view(const float *smem, int col, int W, float fc, float ur0, float dur, float rmax,
                                         float inv_v, float kf, const float *lo, const float *hi, float *acc)
 {
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
-        const float ur = fminf(fmaxf(fmaf((float)t, dur, ur0), 0.0f), rmax);
-        const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur)
-        const int ri = __float_as_int(yv) - 0x4B000000;
+        float om = 1.0f;
+        if (WEIGHTED) {
+            om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
+            if (om == 0.0f) continue;
+        }
+        float ur = fmaf((float)t, dur, ur0);
+        if (CLAMP) ur = fminf(fmaxf(ur, 0.0f), rmax);
+        const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur), ur >= 0
+        const int q = col + (__float_as_int(yv) - 0x4B000000) * W;
         const float fr = ur - (yv - 8388608.0f);
-        const float *q = col + ri * W;
-        const float v00 = q[0], v01 = q[1], v10 = q[W], v11 = q[W + 1];
+        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + W], v11 = smem[q + W + 1];
         const float top = fmaf(fc, v01 - v00, v00);
         const float bot = fmaf(fc, v11 - v10, v10);
         const float val = fmaf(fr, bot - top, top);
-        if (WEIGHTED) {
-            const float om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
-            acc[t] = fmaf(om * inv_v, val, acc[t]);
-        } else {
-            acc[t] = fmaf(inv_v, val, acc[t]);
-        }
+        acc[t] = fmaf(WEIGHTED ? om * inv_v : inv_v, val, acc[t]);
     }
 }
 
+template <bool POLY, bool ROWS_OK>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
-    extern __shared__ __align__(128) unsigned char s_raw[];
-    // [B2_R][slot_floats], base rounded up to 128 bytes (TMA destinations)
-    float *const s_views = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(s_raw) + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t s_full[B2_R], s_empty[B2_R];
     __shared__ int s_col[B2_R];
-    __shared__ int s_K0, s_K1, s_abort;
+    __shared__ int s_K0, s_K1;
     const BPArgs &a = p.a;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -240,6 +256,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
     const int s0 = blockIdx.z * B2_T;
     const bool active = !producer && ix < a.nx && iy < a.ny;
+    // slots start at the first 128-byte boundary of the dynamic shared memory (TMA destinations)
+    const int base = (int)(((128u - (smem_addr(smem) & 127u)) & 127u) >> 2);
 
     // per-slice view windows; weights omega(k) = sat(k - lo_t) * sat(hi_t - k) relative to kbase
     int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
@@ -283,7 +301,6 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     if (tid == 0) {
         s_K0 = INT32_MAX;
         s_K1 = INT32_MIN;
-        s_abort = 0;
         for (int r = 0; r < B2_R; ++r) {
             mbar_init(&s_full[r], 1);
             mbar_init(&s_empty[r], B2_CW);
@@ -308,17 +325,20 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
         const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
         const uint32_t box_bytes = (uint32_t)(p.W * p.srows * 4);
-        int issued = 0;
+        const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
+        int slot = 0, issued = 0;
+        uint32_t phase = 0;
+        int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
+        bool ok = true;
         for (int j = 0; j < nviews; ++j) {
-            const int slot = j % B2_R, use = j / B2_R;
-            if (use > 0 && !mbar_wait(&s_empty[slot], (uint32_t)((use - 1) & 1))) {
-                if (lane == 0) atomicOr(&s_abort, 1);
+            if (j >= B2_R && !mbar_wait(&s_empty[slot], phase ^ 1u)) {
+                ok = false;
                 break;
             }
-            if (*((volatile int *)&s_abort)) break;
-            const int k = K0 + j;
-            const int kmod = ((k % a.vpt) + a.vpt) % a.vpt;
-            float c = column_of(a, __ldg(a.trig + kmod), cx, cy);
+            const float2 cs = __ldg(a.trig + kmod);
+            const float v = a.R - cx * cs.x - cy * cs.y;
+            const float u = -cx * cs.y + cy * cs.x;
+            float c = column_coord<POLY>(a, u * (1.0f / v));
             c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
             c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
             if (lane == 0) {
@@ -326,13 +346,18 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 const int clo = ((int)floorf(c) - 1) & ~3;
                 s_col[slot] = clo;
                 mbar_arrive_expect_tx(&s_full[slot], box_bytes);
-                tma_load_3d(s_views + (size_t)slot * p.slot_floats, &gmap, &s_full[slot], clo, -1,
-                            k - (int)a.first_view);
+                tma_load_3d(dst0 + 4u * (uint32_t)(slot * p.slot_floats), &gmap, &s_full[slot], clo, -1,
+                            K0 + j - (int)a.first_view);
             }
             __syncwarp();
             issued = j + 1;
+            if (++slot == B2_R) {
+                slot = 0;
+                phase ^= 1u;
+            }
+            if (++kmod == a.vpt) kmod = 0;
         }
-        if (lane == 0 && *((volatile int *)&s_abort)) {
+        if (!ok && lane == 0) {
             // let every issued copy land before the CTA's shared memory is released
             for (int j = max(0, issued - B2_R); j < issued; ++j)
                 mbar_wait(&s_full[j % B2_R], (uint32_t)((j / B2_R) & 1));
@@ -349,39 +374,41 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const float hdl = (float)(a.h * a.dlam);
     const float rmax = (float)(a.n_rows + 1);
     int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;  // view index mod views_per_turn
+    int slot = 0;
+    uint32_t phase = 0;
     for (int j = 0; j < nviews; ++j) {
-        const int slot = j % B2_R;
         const int k = K0 + j;
-        const int km = kmod;
-        kmod = (kmod + 1 == a.vpt) ? 0 : kmod + 1;
-        if (!mbar_wait(&s_full[slot], (uint32_t)((j / B2_R) & 1))) {
-            if (lane == 0) atomicOr(&s_abort, 1);
-            break;
+        if (!mbar_wait(&s_full[slot], phase)) {
+            if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
+            return;  // the producer's own bounded waits end the CTA
         }
         if (active && k >= kmin && k <= kmax) {
-            const float *sl = s_views + (size_t)slot * p.slot_floats;
-            const float2 cs = __ldg(a.trig + km);
+            const float2 cs = __ldg(a.trig + kmod);
             const float v = a.R - x * cs.x - y * cs.y;
             const float u = -x * cs.y + y * cs.x;
-            const float inv_v = 1.0f / v;
-            const float uc = (atanf(u * inv_v) - a.alpha0) * a.inv_da - (float)s_col[slot];
+            const float inv_v = __frcp_rn(v);
+            const float uc = column_coord<POLY>(a, u * inv_v) - (float)s_col[slot];
             const float cf = floorf(uc);
             const float fc = uc - cf;
-            const int ci = min(max((int)cf, 0), p.W - 2);
-            const float M = a.D * rsqrtf(u * u + v * v);  // D cos(alpha*) / v*
+            const int col = base + slot * p.slot_floats + min(max((int)cf, 0), p.W - 2);
+            const float M = a.D * rsqrtf(fmaf(u, u, v * v));  // D cos(alpha*) / v*
             const float kf = (float)(k - kbase);
-            const float ur0 = (M * (zb - hdl * kf) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
+            const float ur0 = (M * fmaf(-hdl, kf, zb) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
             const float dur = M * a.dz_over_dw;
             if (k > kfull_lo && k < kfull_hi)
-                bp_view<false>(sl + ci, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<false, !ROWS_OK>(smem, col, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
             else
-                bp_view<true>(sl + ci, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<true, true>(smem, col, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[slot]);
-        if (*((volatile int *)&s_abort)) break;
+        if (++slot == B2_R) {
+            slot = 0;
+            phase ^= 1u;
+        }
+        if (++kmod == a.vpt) kmod = 0;
     }
-    if (!active || *((volatile int *)&s_abort)) return;
+    if (!active) return;
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
         const int s = s0 + t;
@@ -485,10 +512,18 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r == CUDA_SUCCESS) {
             BP2Args b{a, W, srows, slot, p.dev_status};
-            KATS_CUDA(cudaFuncSetAttribute(k_backproject_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
+            const bool poly = p.r_fov <= p.g.R * 0.70710678;
+            // every contributing row within half a row of the detector (plan extents, FP32 on device)
+            const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
+            const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
+            const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
+            auto kern = poly ? (rows_ok ? k_backproject_tma<true, true> : k_backproject_tma<true, false>)
+                             : (rows_ok ? k_backproject_tma<false, true> : k_backproject_tma<false, false>);
+            KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
                       (unsigned)ceil_div(p.g.nz, B2_T));
-            k_backproject_tma<<<grid, B2_THREADS, smem, st>>>(map, b);
+            kern<<<grid, B2_THREADS, smem, st>>>(map, b);
             KATS_CUDA(cudaGetLastError());
             return KATS_OK;
         }

@@ -22,6 +22,7 @@ struct Plan {
     int64_t n_psi;    // kappa lines
     int64_t nc1;      // half-grid columns (n_cols - 1)
     double alpha_m, psi_max, dpsi, h, dlam;
+    double r_fov;  // farthest volume corner from the axis
     int64_t first_view, n_fviews;  // filtered half-views the volume needs
     int64_t gf_cols;               // row pitch of g^F in floats: n_cols rounded up to 4 (16-byte rows)
     int64_t update_count;

@@ -611,7 +611,8 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->N = N;
     p->n_psi = g->n_psi > 0 ? g->n_psi : 2 * g->n_rows;
     p->nc1 = g->n_cols - 1;
-    p->alpha_m = asin(r_fov(*g) / g->R);
+    p->r_fov = r_fov(*g);
+    p->alpha_m = asin(p->r_fov / g->R);
     p->psi_max = 0.5 * kPi + p->alpha_m;
     p->dpsi = 2.0 * p->psi_max / (double)(p->n_psi - 1);
     p->h = g->P / (2.0 * kPi);
