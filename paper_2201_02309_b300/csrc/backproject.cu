@@ -142,7 +142,7 @@ __constant__ float c_atan[kAtanTerms] = {2.456725342e-03f, -1.440136135e-02f, 3.
 
 struct BP2Args {
     BPArgs a;
-    int W;            // staged columns per view (multiple of 4)
+    int W;            // columns of the staged box any voxel of the tile can touch (<= PITCH)
     int srows;        // staged rows: n_rows + 3 (row 0 and rows n_rows+1.. are zero fill)
     int slot_floats;  // floats per staged view, multiple of 32 (128-byte slots)
     int *status;
@@ -211,15 +211,17 @@ __device__ __forceinline__ float column_coord(const BPArgs &a, float t)
 }
 
 // One view's contribution to a thread's B2_T slices, reading taps from
-// smem[col + row * W].  WEIGHTED: the view ends some slice's PI window (end
-// weights, or zero outside it); otherwise every slice takes it with weight 1.
-// CLAMP: keep the row inside the staged window (needed whenever a slice can be
-// outside its PI window or the plan cannot prove rows stay within one row of
-// the detector).
-template <bool WEIGHTED, bool CLAMP>
-__device__ __forceinline__ void bp_view(const float *smem, int col, int W, float fc, float ur0, float dur, float rmax,
+// smem[colx + (row << log2 PITCH)] (colx carries the -2^23 row-bias of the
+// floor trick, in modulo-2^32 arithmetic).  WEIGHTED: the view ends some
+// slice's PI window (end weights, or zero outside it); otherwise every slice
+// takes it with weight 1.  CLAMP: keep the row inside the staged window
+// (needed whenever a slice can be outside its PI window or the plan cannot
+// prove rows stay within one row of the detector).
+template <int PITCH, bool WEIGHTED, bool CLAMP>
+__device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
                                         float inv_v, float kf, const float *lo, const float *hi, float *acc)
 {
+    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
         float om = 1.0f;
@@ -230,9 +232,9 @@ __device__ __forceinline__ void bp_view(const float *smem, int col, int W, float
         float ur = fmaf((float)t, dur, ur0);
         if (CLAMP) ur = fminf(fmaxf(ur, 0.0f), rmax);
         const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur), ur >= 0
-        const int q = col + (__float_as_int(yv) - 0x4B000000) * W;
+        const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
         const float fr = ur - (yv - 8388608.0f);
-        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + W], v11 = smem[q + W + 1];
+        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + PITCH], v11 = smem[q + PITCH + 1];
         const float top = fmaf(fc, v01 - v00, v00);
         const float bot = fmaf(fc, v11 - v10, v10);
         const float val = fmaf(fr, bot - top, top);
@@ -240,13 +242,21 @@ __device__ __forceinline__ void bp_view(const float *smem, int col, int W, float
     }
 }
 
-template <bool POLY, bool ROWS_OK>
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int PITCH, bool POLY, bool ROWS_OK>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t s_full[B2_R], s_empty[B2_R];
     __shared__ int s_col[B2_R];
+    __shared__ float2 s_cs[B2_R];
     __shared__ int s_K0, s_K1;
     const BPArgs &a = p.a;
     const int tid = threadIdx.x;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         // is extremal at them (u*/v* is linear-fractional in (x, y))
         const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
         const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
-        const uint32_t box_bytes = (uint32_t)(p.W * p.srows * 4);
+        const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
         const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
         int slot = 0, issued = 0;
         uint32_t phase = 0;
@@ -345,6 +355,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 // one column of slack left of the lowest tap, start aligned to 4 floats (16 bytes)
                 const int clo = ((int)floorf(c) - 1) & ~3;
                 s_col[slot] = clo;
+                s_cs[slot] = cs;
                 mbar_arrive_expect_tx(&s_full[slot], box_bytes);
                 tma_load_3d(dst0 + 4u * (uint32_t)(slot * p.slot_floats), &gmap, &s_full[slot], clo, -1,
                             K0 + j - (int)a.first_view);
@@ -373,7 +384,6 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                              a.h * (a.lambda_first + ((double)kbase + 0.5) * a.dlam));
     const float hdl = (float)(a.h * a.dlam);
     const float rmax = (float)(a.n_rows + 1);
-    int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;  // view index mod views_per_turn
     int slot = 0;
     uint32_t phase = 0;
     for (int j = 0; j < nviews; ++j) {
@@ -383,22 +393,24 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             return;  // the producer's own bounded waits end the CTA
         }
         if (active && k >= kmin && k <= kmax) {
-            const float2 cs = __ldg(a.trig + kmod);
+            const float2 cs = s_cs[slot];
             const float v = a.R - x * cs.x - y * cs.y;
             const float u = -x * cs.y + y * cs.x;
-            const float inv_v = __frcp_rn(v);
+            const float inv_v = rcp_approx(v);
             const float uc = column_coord<POLY>(a, u * inv_v) - (float)s_col[slot];
             const float cf = floorf(uc);
             const float fc = uc - cf;
-            const int col = base + slot * p.slot_floats + min(max((int)cf, 0), p.W - 2);
+            constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
+            const uint32_t colx = (uint32_t)(base + slot * p.slot_floats + min(max((int)cf, 0), p.W - 2)) -
+                                  (0x4B000000u << SH);
             const float M = a.D * rsqrtf(fmaf(u, u, v * v));  // D cos(alpha*) / v*
             const float kf = (float)(k - kbase);
             const float ur0 = (M * fmaf(-hdl, kf, zb) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
             const float dur = M * a.dz_over_dw;
             if (k > kfull_lo && k < kfull_hi)
-                bp_view<false, !ROWS_OK>(smem, col, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<PITCH, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
             else
-                bp_view<true, true>(smem, col, p.W, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<PITCH, true, true>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[slot]);
@@ -406,7 +418,6 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             slot = 0;
             phase ^= 1u;
         }
-        if (++kmod == a.vpt) kmod = 0;
     }
     if (!active) return;
 #pragma unroll
@@ -489,45 +500,55 @@ static int window_cols(const Plan &p)
     return ((int)ceil(span) + 8 + 3) / 4 * 4;
 }
 
+template <int PITCH>
+static int launch_tma(const Plan &p, const BPArgs &a, const float *gF, int W, cudaStream_t st, bool *launched)
+{
+    *launched = false;
+    const int srows = (int)p.g.n_rows + 3;
+    const int slot = (PITCH * srows + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * (size_t)slot * B2_R + 128;  // + base alignment slack
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || W > PITCH || PITCH > p.gf_cols || srows > 256 || smem > 200 * 1024 ||
+        (reinterpret_cast<uintptr_t>(gF) % 16) != 0 || p.n_fviews >= INT32_MAX)
+        return KATS_OK;
+    CUtensorMap map;
+    cuuint64_t dims[3] = {(cuuint64_t)p.gf_cols, (cuuint64_t)p.g.n_rows, (cuuint64_t)p.n_fviews};
+    cuuint64_t strides[2] = {(cuuint64_t)p.gf_cols * 4, (cuuint64_t)(p.gf_cols * p.g.n_rows) * 4};
+    cuuint32_t box[3] = {(cuuint32_t)PITCH, (cuuint32_t)srows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)gF, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return KATS_OK;
+    BP2Args b{a, W, srows, slot, p.dev_status};
+    // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
+    const bool poly = p.r_fov <= p.g.R * 0.70710678;
+    // every contributing row within half a row of the detector (plan extents, FP32 on device)
+    const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
+    const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
+    const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
+    auto kern = poly ? (rows_ok ? k_backproject_tma<PITCH, true, true> : k_backproject_tma<PITCH, true, false>)
+                     : (rows_ok ? k_backproject_tma<PITCH, false, true> : k_backproject_tma<PITCH, false, false>);
+    KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY), (unsigned)ceil_div(p.g.nz, B2_T));
+    kern<<<grid, B2_THREADS, smem, st>>>(map, b);
+    KATS_CUDA(cudaGetLastError());
+    *launched = true;
+    return KATS_OK;
+}
+
 int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st)
 {
     BPArgs a = bp_args(p);
     a.gF = gF;
     a.vol = vol;
     const int W = window_cols(p);
-    const int srows = (int)p.g.n_rows + 3;
-    const int slot = (W * srows + 31) / 32 * 32;
-    const size_t smem = sizeof(float) * (size_t)slot * B2_R + 128;  // + base alignment slack
-    EncodeTiledFn enc = encode_fn();
-    const bool tma_ok = enc && W <= 256 && W <= p.gf_cols && srows <= 256 && smem <= 200 * 1024 &&
-                        (reinterpret_cast<uintptr_t>(gF) % 16) == 0 && p.n_fviews < INT32_MAX;
-    if (tma_ok) {
-        CUtensorMap map;
-        cuuint64_t dims[3] = {(cuuint64_t)p.gf_cols, (cuuint64_t)p.g.n_rows, (cuuint64_t)p.n_fviews};
-        cuuint64_t strides[2] = {(cuuint64_t)p.gf_cols * 4, (cuuint64_t)(p.gf_cols * p.g.n_rows) * 4};
-        cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)srows, 1};
-        cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)gF, dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS) {
-            BP2Args b{a, W, srows, slot, p.dev_status};
-            // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
-            const bool poly = p.r_fov <= p.g.R * 0.70710678;
-            // every contributing row within half a row of the detector (plan extents, FP32 on device)
-            const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
-            const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
-            const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
-            auto kern = poly ? (rows_ok ? k_backproject_tma<true, true> : k_backproject_tma<true, false>)
-                             : (rows_ok ? k_backproject_tma<false, true> : k_backproject_tma<false, false>);
-            KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
-                      (unsigned)ceil_div(p.g.nz, B2_T));
-            kern<<<grid, B2_THREADS, smem, st>>>(map, b);
-            KATS_CUDA(cudaGetLastError());
-            return KATS_OK;
-        }
-    }
+    bool launched = false;
+    int rc = KATS_OK;
+    if (W <= 32) rc = launch_tma<32>(p, a, gF, W, st, &launched);
+    else if (W <= 64) rc = launch_tma<64>(p, a, gF, W, st, &launched);
+    else if (W <= 128) rc = launch_tma<128>(p, a, gF, W, st, &launched);
+    if (rc || launched) return rc;
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
     k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);
     KATS_CUDA(cudaGetLastError());
