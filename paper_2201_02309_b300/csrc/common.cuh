@@ -36,6 +36,11 @@ struct Plan {
     float *pi_w0 = nullptr, *pi_w1 = nullptr;    // [N][ny][nx]
     int32_t *slice_kmin = nullptr, *slice_kmax = nullptr;  // [N] per table slice
     float *hk = nullptr;    // Hilbert kernel, [2 n_cols - 2], entry n + n_cols - 2 for n = c - c'
+    // Toeplitz operand of the tensor-core Hilbert step: Bt[c][c'] = hk(c - c') for c < n_cols,
+    // c' < n_cols - 1 (zero elsewhere), split as hi = value with the low 13 mantissa bits cleared
+    // (exact in TF32) and lo = value - hi; [tc_n][tc_k] row-major.
+    float *bt_hi = nullptr, *bt_lo = nullptr;
+    int64_t tc_k = 0, tc_n = 0;  // K padded to 32, N padded to 256
     float *lw = nullptr;    // [n_rows] length-correction weight
     float *cosa = nullptr;  // [n_cols] cos(alpha_c)
     float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
@@ -67,6 +72,8 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
 int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes,
                           cudaStream_t st);
 size_t filter_workspace_bytes(const Plan &p);
+// tensor-core Hilbert step (hilbert_tc.cu); *done = false when it cannot run
+int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done);
 size_t filter_adjoint_workspace_bytes(const Plan &p);
 
 }  // namespace kats

@@ -14,13 +14,15 @@
 
 namespace kats {
 
-// Padded K extent of the g3 rows (multiple of 16 floats, zero tail).
-static inline int64_t kpad(const Plan &p) { return (p.nc1 + 15) / 16 * 16; }
+// Padded K extent of the g3 rows (multiple of 32 floats = one 128-byte
+// tensor-core K block, zero tail).
+static inline int64_t kpad(const Plan &p) { return p.tc_k; }
 
+// g4 rows are padded to tc_n (whole tensor-core N tiles).
 size_t filter_workspace_bytes(const Plan &p)
 {
     const int64_t nv = p.n_fviews;
-    return sizeof(float) * (size_t)(nv * p.n_psi * kpad(p) + nv * p.n_psi * p.g.n_cols);
+    return sizeof(float) * (size_t)(nv * p.n_psi * kpad(p) + nv * p.n_psi * p.tc_n);
 }
 
 // ---------------------------------------------------------------- steps 1-3
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(256) k_toeplitz_gemm(const float *__restrict__
 // gF rows have pitch gcols >= n_cols; the pad columns are written as zeros.
 __global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ gF, const int32_t *__restrict__ psi_idx,
                               const float *__restrict__ psi_frac, const float *__restrict__ cosa, int64_t nv,
-                              int n_rows, int n_cols, int n_psi, int gcols)
+                              int n_rows, int n_cols, int n_psi, int gcols, int ld4)
 {
     const int64_t per = (int64_t)n_rows * gcols;
     const int64_t total = nv * per;
@@ -151,9 +153,9 @@ __global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ 
         const int rc = r * n_cols + c;
         const int l = psi_idx[rc];
         const float f = psi_frac[rc];
-        const float *col = g4 + v * n_psi * n_cols + c;
-        const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * n_cols] : 0.0f;
-        const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * n_cols] : 0.0f;
+        const float *col = g4 + v * n_psi * ld4 + c;
+        const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
+        const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
         gF[t] = cosa[c] * ((1.0f - f) * lo + f * hi);
     }
 }
@@ -175,16 +177,22 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
                                          (int)np, (int)Kp, a_lam, a_alp);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
-    if (ceil_div(M, GBM) > 65535) {
-        set_error("too many filtered views for one launch (%lld)", (long long)nv);
-        return KATS_EINVAL;
+    const int ld4 = (int)p.tc_n;
+    bool tc = false;
+    int rc = launch_hilbert_tc(p, g3, g4, M, ld4, st, &tc);
+    if (rc) return rc;
+    if (!tc) {
+        if (ceil_div(M, GBM) > 65535) {
+            set_error("too many filtered views for one launch (%lld)", (long long)nv);
+            return KATS_EINVAL;
+        }
+        dim3 g2((unsigned)ceil_div(nc, GBN), (unsigned)ceil_div(M, GBM));
+        k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, ld4, (int)nc, 0);
+        KATS_CUDA(cudaGetLastError());
     }
-    dim3 g2((unsigned)ceil_div(nc, GBN), (unsigned)ceil_div(M, GBM));
-    k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, (int)nc, (int)nc, 0);
-    KATS_CUDA(cudaGetLastError());
     const int64_t total = nv * nr * p.gf_cols;
     k_unrebin_cos<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
-        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols);
+        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols, ld4);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }

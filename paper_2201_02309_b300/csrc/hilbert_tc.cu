@@ -1,0 +1,347 @@
+// Step 4 of the reconstruction step (Sec. II, Eq. (HF)): the Hilbert
+// transform in alpha at constant psi, as a Toeplitz contraction on the 5th
+// generation tensor cores:
+//     g4[m][c] = sum_{c'} g3[m][c'] T[c'][c],   T[c'][c] = hk(c - c'),
+// m = (filtered view, psi line), c' = half-grid column, c = column.
+//
+// FP32 accuracy from TF32 operands (3xTF32): A = A_hi + A_lo and
+// T = T_hi + T_lo with hi exact in TF32 (low 13 mantissa bits cleared), and
+//     C = A_hi T_hi + A_hi T_lo + A_lo T_hi
+// (the dropped A_lo T_lo term is ~2^-22 of the product).  T_hi / T_lo are
+// plan constants; A is split in place in shared memory.
+//
+// One CTA computes a 128 x 256 tile of C in TMEM:
+//   warp 0      TMA producer (A tile 128 x 32, T_hi / T_lo tiles 256 x 32,
+//               fp32, 128-byte swizzle), 2-stage ring
+//   warp 1      TMEM allocation and the single-thread tcgen05.mma issuer
+//   warps 2..5  split A into hi / lo in shared memory, then the epilogue
+//               (tcgen05.ld -> registers -> global g4)
+// Every mbarrier wait is bounded; on a timeout the CTA records a device
+// status, drains its own copies and frees TMEM before returning.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace kats {
+
+namespace {
+
+constexpr int TC_M = 128, TC_N = 256, TC_K = 32;  // tile; K block = one 128-byte swizzle span
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_A_BYTES = TC_M * TC_K * 4;  // 16 KB
+constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 4;  // 32 KB
+constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // A, A_lo, T_hi, T_lo
+constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;       // + alignment slack
+constexpr int kTcWaitLimit = 1 << 22;
+
+// Instruction descriptor, kind::tf32: D fp32 (bits 4-5 = 1), A and B tf32
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                                ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity)
+{
+    for (int i = 0; i < kTcWaitLimit; ++i)
+        if (bar_try(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, uint64_t *b, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(b))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes, 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1 (bits 46-47), layout type 2 = 128-byte swizzle (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kIdescTf32), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive fp32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+    float *C;  // [M][ldc], ldc a multiple of TC_N (whole tiles are stored)
+    int64_t M;
+    int ldc, kblocks;
+    int *status;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_hilbert_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
+                 const __grid_constant__ CUtensorMap mapBl, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t s_full[TC_STAGES], s_conv[TC_STAGES], s_empty[TC_STAGES], s_acc;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_issued;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (saddr(tc_raw) + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
+    unsigned char *const gbase = tc_raw + (base - saddr(tc_raw));
+    const int64_t m0 = (int64_t)blockIdx.y * TC_M;
+    const int n0 = blockIdx.x * TC_N;
+    auto stA = [&](int s) { return base + (uint32_t)s * TC_STAGE_BYTES; };
+    auto stAlo = [&](int s) { return stA(s) + TC_A_BYTES; };
+    auto stBh = [&](int s) { return stA(s) + 2 * TC_A_BYTES; };
+    auto stBl = [&](int s) { return stA(s) + 2 * TC_A_BYTES + TC_B_BYTES; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            bar_init(&s_full[s], 1);
+            bar_init(&s_conv[s], 4);
+            bar_init(&s_empty[s], 1);
+        }
+        bar_init(&s_acc, 1);
+        s_abort = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"((uint32_t)TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    const int nkb = a.kblocks;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (kb >= TC_STAGES && !bar_wait(&s_empty[s], (uint32_t)(((kb >> 1) - 1) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                bar_expect(&s_full[s], TC_A_BYTES + 2 * TC_B_BYTES);
+                tma_2d(stA(s), &mapA, &s_full[s], kb * TC_K, (int)m0);
+                tma_2d(stBh(s), &mapBh, &s_full[s], kb * TC_K, n0);
+                tma_2d(stBl(s), &mapBl, &s_full[s], kb * TC_K, n0);
+                s_issued = kb + 1;
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (!bar_wait(&s_conv[s], (uint32_t)((kb >> 1) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                fence_after();
+#pragma unroll
+                for (int kk = 0; kk < TC_K / 8; ++kk) {  // 8 tf32 = 32 bytes per MMA
+                    const uint32_t off = (uint32_t)kk * 32u;
+                    const uint64_t dA = sw128_desc(stA(s) + off), dAl = sw128_desc(stAlo(s) + off);
+                    const uint64_t dBh = sw128_desc(stBh(s) + off), dBl = sw128_desc(stBl(s) + off);
+                    mma_tf32(tmem, dA, dBh, (kb | kk) != 0);
+                    mma_tf32(tmem, dA, dBl, 1u);
+                    mma_tf32(tmem, dAl, dBh, 1u);
+                }
+                mma_commit(&s_empty[s]);  // stage s free once these MMAs have read it
+            }
+            mma_commit(&s_acc);  // accumulator complete (or abandoned on abort)
+        }
+    } else {
+        // ---------------- converters (warps 2..5), then epilogue
+        const int ct = threadIdx.x - 64;  // 0..127
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1;
+            if (!bar_wait(&s_full[s], (uint32_t)((kb >> 1) & 1))) {
+                atomicExch(&s_abort, 1);
+                break;
+            }
+            if (*(volatile int *)&s_abort) break;
+            // element-wise split, independent of the swizzled layout: hi in place, lo alongside
+            float4 *A = reinterpret_cast<float4 *>(gbase + (stA(s) - base));
+            float4 *L = reinterpret_cast<float4 *>(gbase + (stAlo(s) - base));
+#pragma unroll
+            for (int i = 0; i < (int)(TC_A_BYTES / 16) / 128; ++i) {
+                const int e = ct + 128 * i;
+                float4 v = A[e], h, l;
+                h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                l.x = v.x - h.x;
+                l.y = v.y - h.y;
+                l.z = v.z - h.z;
+                l.w = v.w - h.w;
+                A[e] = h;
+                L[e] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+            __syncwarp();
+            if (lane == 0) bar_arrive(&s_conv[s]);
+        }
+        // epilogue: TMEM lane = tile row; warp w may read lanes 32 (w % 4) .. + 31
+        const bool done = bar_wait(&s_acc, 0u);
+        if (!done) atomicExch(&s_abort, 1);
+        fence_after();
+        if (done && !*(volatile int *)&s_abort) {
+            const int quarter = warp & 3;
+            const int64_t row = m0 + quarter * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+            for (int cb = 0; cb < TC_N / 32; ++cb) {
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)(cb * 32), v);
+                if (row < a.M) {
+                    float4 *out = reinterpret_cast<float4 *>(a.C + row * a.ldc + n0 + cb * 32);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
+        }
+    }
+
+    // ---------------- teardown
+    fence_before();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        // drain the producer's copies (the last TC_STAGES issued) before shared memory is released
+        for (int kb = max(0, s_issued - TC_STAGES); kb < s_issued; ++kb)
+            bar_wait(&s_full[kb & 1], (uint32_t)((kb >> 1) & 1));
+        atomicExch(a.status, kDevStatusTimeout);
+    }
+    if (warp == 1) {
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_N)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder()
+{
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)ptr;
+    });
+    return fn;
+}
+
+bool encode_2d(EncodeFn enc, CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, int box_inner,
+               int box_outer)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// g4[M][ldc] = g3[M][tc_k] . T on the tensor cores (ldc a multiple of 256).
+// Returns KATS_OK with *done = false when the tensor-core path cannot run
+// (no tensor-map encoder, misaligned buffers), leaving the caller to fall back.
+int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done)
+{
+    *done = false;
+    EncodeFn enc = encoder();
+    if (!enc || M < 1 || ldc % TC_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(g4) % 16) != 0 || ceil_div(M, TC_M) > 65535)
+        return KATS_OK;
+    CUtensorMap mA, mBh, mBl;
+    if (!encode_2d(enc, &mA, g3, p.tc_k, M, TC_K, TC_M) || !encode_2d(enc, &mBh, p.bt_hi, p.tc_k, p.tc_n, TC_K, TC_N) ||
+        !encode_2d(enc, &mBl, p.bt_lo, p.tc_k, p.tc_n, TC_K, TC_N))
+        return KATS_OK;
+    TcArgs a{g4, M, ldc, (int)(p.tc_k / TC_K), p.dev_status};
+    KATS_CUDA(cudaFuncSetAttribute(k_hilbert_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
+    k_hilbert_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mBh, mBl, a);
+    KATS_CUDA(cudaGetLastError());
+    *done = true;
+    return KATS_OK;
+}
+
+}  // namespace kats

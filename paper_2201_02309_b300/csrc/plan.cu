@@ -426,7 +426,8 @@ static void free_plan(Plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
-                    p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status};
+                    p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status,
+                    p->bt_hi, p->bt_lo};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -456,7 +457,8 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->pi_w0, N * nxy)) || (rc = dalloc(p, &p->pi_w1, N * nxy)) ||
         (rc = dalloc(p, &p->slice_kmin, N)) || (rc = dalloc(p, &p->slice_kmax, N)) ||
         (rc = dalloc(p, &p->hk, 2 * nc - 2)) || (rc = dalloc(p, &p->lw, nr)) || (rc = dalloc(p, &p->cosa, nc)) ||
-        (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->dev_status, 1)))
+        (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->dev_status, 1)) ||
+        (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)))
         return rc;
     KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
 
@@ -479,6 +481,20 @@ static int build(Plan *p)
         KATS_CUDA(cudaMemcpy(p->lw, lw.data(), lw.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->cosa, cosa.data(), cosa.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        std::vector<float> bhi((size_t)(p->tc_n * p->tc_k), 0.0f), blo((size_t)(p->tc_n * p->tc_k), 0.0f);
+        for (int64_t c = 0; c < nc; ++c)
+            for (int64_t cp = 0; cp < p->nc1; ++cp) {
+                const float v = hk[c - cp + nc - 2];
+                uint32_t bits;
+                std::memcpy(&bits, &v, 4);
+                bits &= 0xFFFFE000u;
+                float hi;
+                std::memcpy(&hi, &bits, 4);
+                bhi[(size_t)(c * p->tc_k + cp)] = hi;
+                blo[(size_t)(c * p->tc_k + cp)] = v - hi;
+            }
+        KATS_CUDA(cudaMemcpy(p->bt_hi, bhi.data(), bhi.size() * sizeof(float), cudaMemcpyHostToDevice));
+        KATS_CUDA(cudaMemcpy(p->bt_lo, blo.data(), blo.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
 
     k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256>>>(G, p->kap_idx, p->kap_frac);
@@ -618,6 +634,8 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->h = g->P / (2.0 * kPi);
     p->dlam = 2.0 * kPi / (double)g->views_per_turn;
     p->gf_cols = (g->n_cols + 3) / 4 * 4;
+    p->tc_k = (p->nc1 + 31) / 32 * 32;
+    p->tc_n = (g->n_cols + 255) / 256 * 256;
     rc = build(p);
     if (rc) {
         free_plan(p);
