@@ -220,6 +220,12 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- ours
+def job_throughput(ms_local, updates_per_rank, world, max_over_ranks):
+    """Whole-job GUPS: every rank's updates over the slowest rank's time."""
+    ms = max_over_ranks(ms_local)
+    return ms, updates_per_rank * world / (ms / 1e3) / 1e9
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -275,9 +281,8 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    ms, value = job_throughput(e0.elapsed_time(e1) / args.steps, info["update_count"], world, max_over_ranks)
     updates = info["update_count"] * world
-    value = updates / (ms / 1e3) / 1e9
 
     # per-kernel durations over the same work (events on the launching stream)
     gF = torch.empty(plan.filtered_shape, dtype=torch.float32, device=dev)

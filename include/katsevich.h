@@ -179,6 +179,21 @@ KATS_API int katsevich_filter(const kats_plan *plan, const float *sino, float *g
 KATS_API int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, int batch, void *stream);
 
 /*
+ * Transpose of step 7 alone: vol [batch][nz][ny][nx] -> gF [batch][n_filtered_views][n_rows][gf_cols]
+ * (every element written; pad columns 0).  FP32 atomics: the summation order,
+ * and so the last bits, may vary between calls.
+ */
+KATS_API int katsevich_backproject_adjoint(const kats_plan *plan, const float *vol, float *gF, int batch, void *stream);
+
+/*
+ * Transpose of steps 1-6 alone: gF [batch][n_filtered_views][n_rows][gf_cols]
+ * -> sino [batch][n_views][n_rows][n_cols] (every element written).
+ * `workspace` as for katsevich_adjoint.
+ */
+KATS_API int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, float *sino, int batch, int precision,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * End-to-end call with HOST buffers: copies the needed sinogram views from
  * host_sino (pinned memory recommended) to the device, runs katsevich_recon and
  * copies the volume back to host_vol, all on `stream`, then waits for the

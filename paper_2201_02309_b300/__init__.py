@@ -156,6 +156,24 @@ class Plan:
         native.katsevich_backproject(self.handle, gF.data_ptr(), out.data_ptr(), b, _stream_ptr(stream))
         return out
 
+    def backproject_adjoint(self, vol, stream=None):
+        """Transpose of step 7: volume -> filtered-data layout [views][rows][gf_cols]."""
+        torch = _torch()
+        b = self._batch(vol, self.vol_shape)
+        out = torch.empty(vol.shape[:-3] + self.filtered_shape, dtype=torch.float32, device=vol.device)
+        native.katsevich_backproject_adjoint(self.handle, vol.data_ptr(), out.data_ptr(), b, _stream_ptr(stream))
+        return out
+
+    def filter_adjoint(self, gF, precision=KATS_PREC_FP32, stream=None):
+        """Transpose of steps 1-6: filtered-data layout -> sinogram."""
+        torch = _torch()
+        b = self._batch(gF, self.filtered_shape)
+        out = torch.empty(gF.shape[:-3] + self.sino_shape, dtype=torch.float32, device=gF.device)
+        ws = self.workspace(precision, gF.device)
+        native.katsevich_filter_adjoint(self.handle, gF.data_ptr(), out.data_ptr(), b, precision, ws.data_ptr(),
+                                        ws.numel() * ws.element_size(), _stream_ptr(stream))
+        return out
+
     def recon_host(self, host_sino, host_vol, batch=1, precision=KATS_PREC_FP32, stream=None, workspace=None):
         """End-to-end call on host (ideally pinned) torch CPU tensors; synchronous."""
         torch = _torch()

@@ -139,6 +139,39 @@ int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, float *sino_
     return KATS_OK;
 }
 
+int katsevich_backproject_adjoint(const kats_plan *plan, const float *vol, float *gF, int batch, void *stream)
+{
+    if (!plan || !vol || !gF || batch < 1) {
+        set_error("bad argument");
+        return KATS_EINVAL;
+    }
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b = 0; b < batch; ++b) {
+        int rc = launch_backproject_adjoint(p, vol + b * vol_item(p), gF + b * gf_item(p), st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
+int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, float *sino, int batch, int precision,
+                             void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = check_common(plan, gF, sino, batch, precision, workspace);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    if (workspace_bytes < filter_adjoint_workspace_bytes(p)) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, filter_adjoint_workspace_bytes(p));
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b = 0; b < batch; ++b) {
+        rc = launch_filter_adjoint(p, gF + b * gf_item(p), sino + b * sino_item(p), workspace, workspace_bytes, st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
 int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision)
 {
     if (!plan || batch < 1 || precision != KATS_PREC_FP32) return -1;

@@ -34,14 +34,51 @@ struct BPArgs {
     float *vol;       // [nz][ny][nx]
     const int32_t *k0, *k1;
     const float *w0, *w1;
-    const float2 *trig;
+    const float2 *trig, *trig_lo;
     int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
     int64_t first_view;
     float R, D, x0, y0, dx, dy;
     float alpha0, inv_da, w0row, inv_dw, dz_over_dw, scale;
     // FP64 terms for z - z_src: z_first + s dz - z0 - h (lambda_first + (k + 1/2) dl)
     double z_first, dz, z0, h, lambda_first, dlam;
+    float hdl, hdl_lo;  // h dl as float plus its rounding residual
+    float K_hi, K_lo;   // alpha0 / d_alpha as float plus its rounding residual
 };
+
+// Detector column of angle alpha, given p = alpha / d_alpha, as integer ci and
+// fraction fc.  Keeping the large constant alpha0 / d_alpha (hi + lo) out of
+// the rounded fraction bounds the error by about 2 ulp(p) instead of
+// ulp(n_cols / 2): this matters for the transpose, whose splat weights carry
+// the coordinate error times the value itself.
+__device__ __forceinline__ void column_split(const BPArgs &a, float p, int *ci, float *fc)
+{
+    const float cf = floorf((p - a.K_hi) - a.K_lo);
+    *ci = (int)cf;
+    *fc = (p - (cf + a.K_hi)) - a.K_lo;
+}
+
+// Per-view source geometry with the trig table carried as float hi + lo, so
+// u* and v* keep FP32 precision relative to themselves (the table's own
+// rounding would otherwise add ~1e-7 x radius of absolute error).
+__device__ __forceinline__ void view_uv(const BPArgs &a, float2 cs, float2 cl, float x, float y, float *u, float *v)
+{
+    *u = fmaf(-x, cs.y, fmaf(y, cs.x, fmaf(-x, cl.y, y * cl.x)));
+    *v = fmaf(-x, cs.x, fmaf(-y, cs.y, fmaf(-x, cl.x, fmaf(-y, cl.y, a.R))));
+}
+
+// z_s - z_src(kbase + kf) for a thread whose slice offset at kbase is zb + zb_lo.
+__device__ __forceinline__ float z_rel(const BPArgs &a, float zb, float zb_lo, float kf)
+{
+    return fmaf(-a.hdl, kf, zb) + fmaf(-a.hdl_lo, kf, zb_lo);
+}
+
+// zb (float) and its residual for slice s0 and view kbase.
+__device__ __forceinline__ void z_base(const BPArgs &a, int s0, int kbase, float *zb, float *zb_lo)
+{
+    const double z = a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kbase + 0.5) * a.dlam);
+    *zb = (float)z;
+    *zb_lo = (float)(z - (double)*zb);
+}
 
 __device__ __forceinline__ float tap(const float *view, int r, int c, int n_rows, int n_cols, int gcols)
 {
@@ -79,25 +116,22 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     }
     const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
     // z_{s0} - z_src(kmin) in FP64 once; later views subtract h dl (k - kmin)
-    const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kmin + 0.5) * a.dlam));
-    const float hdl = (float)(a.h * a.dlam);
+    float zb, zb_lo;
+    z_base(a, s0, kmin, &zb, &zb_lo);
     int km = ((kmin % a.vpt) + a.vpt) % a.vpt;
     const int64_t per_view = (int64_t)a.n_rows * a.gcols;
     for (int k = kmin; k <= kmax; ++k) {
-        const float2 cs = __ldg(a.trig + km);
+        float u, v;
+        view_uv(a, __ldg(a.trig + km), __ldg(a.trig_lo + km), x, y, &u, &v);
         km = (km + 1 == a.vpt) ? 0 : km + 1;
-        const float v = a.R - x * cs.x - y * cs.y;
-        const float u = -x * cs.y + y * cs.x;
         const float inv_v = 1.0f / v;
-        const float alpha = atanf(u * inv_v);
-        const float uc = (alpha - a.alpha0) * a.inv_da;
+        int ci;
+        float fc;
+        column_split(a, atanf(u * inv_v) * a.inv_da, &ci, &fc);
         const float M = a.D * rsqrtf(u * u + v * v);  // D cos(alpha*) / v*
-        const float zr = zb - hdl * (float)(k - kmin);
+        const float zr = z_rel(a, zb, zb_lo, (float)(k - kmin));
         const float ur0 = (M * zr - a.w0row) * a.inv_dw;
         const float dur = M * a.dz_over_dw;
-        const float cf = floorf(uc);
-        const int ci = (int)cf;
-        const float fc = uc - cf;
         const float *view = a.gF + (int64_t)(k - a.first_view) * per_view;
 #pragma unroll
         for (int t = 0; t < BP_T; ++t) {
@@ -196,18 +230,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Detector column coordinate of arctan(t) (t = u*/v*): (atan(t) - alpha0) / d_alpha.
+// arctan(t) / d_alpha (t = u*/v*), the column coordinate before the alpha0 offset.
 template <bool POLY>
-__device__ __forceinline__ float column_coord(const BPArgs &a, float t)
+__device__ __forceinline__ float angle_cols(const BPArgs &a, float t)
 {
     if (POLY) {
         const float s = t * t;
         float p = c_atan[0];
 #pragma unroll
         for (int i = 1; i < kAtanTerms; ++i) p = fmaf(p, s, c_atan[i]);
-        return (t * p - a.alpha0) * a.inv_da;
+        return t * p * a.inv_da;
     }
-    return (atanf(t) - a.alpha0) * a.inv_da;
+    return atanf(t) * a.inv_da;
 }
 
 // One view's contribution to a thread's B2_T slices, reading taps from
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             const float2 cs = __ldg(a.trig + kmod);
             const float v = a.R - cx * cs.x - cy * cs.y;
             const float u = -cx * cs.y + cy * cs.x;
-            float c = column_coord<POLY>(a, u * (1.0f / v));
+            float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
             c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
             c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
             if (lane == 0) {
@@ -380,9 +414,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     // ---------------- consumer warps
     const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
     const int kbase = active ? kmin : 0;
-    const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 -
-                             a.h * (a.lambda_first + ((double)kbase + 0.5) * a.dlam));
-    const float hdl = (float)(a.h * a.dlam);
+    float zb, zb_lo;
+    z_base(a, s0, kbase, &zb, &zb_lo);
     const float rmax = (float)(a.n_rows + 1);
     int slot = 0;
     uint32_t phase = 0;
@@ -394,18 +427,18 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         }
         if (active && k >= kmin && k <= kmax) {
             const float2 cs = s_cs[slot];
-            const float v = a.R - x * cs.x - y * cs.y;
-            const float u = -x * cs.y + y * cs.x;
+            const float v = fmaf(-x, cs.x, fmaf(-y, cs.y, a.R));
+            const float u = fmaf(-x, cs.y, y * cs.x);
             const float inv_v = rcp_approx(v);
-            const float uc = column_coord<POLY>(a, u * inv_v) - (float)s_col[slot];
-            const float cf = floorf(uc);
-            const float fc = uc - cf;
+            int ci;
+            float fc;
+            column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
             constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-            const uint32_t colx = (uint32_t)(base + slot * p.slot_floats + min(max((int)cf, 0), p.W - 2)) -
-                                  (0x4B000000u << SH);
+            const uint32_t colx =
+                (uint32_t)(base + slot * p.slot_floats + min(max(ci - s_col[slot], 0), p.W - 2)) - (0x4B000000u << SH);
             const float M = a.D * rsqrtf(fmaf(u, u, v * v));  // D cos(alpha*) / v*
             const float kf = (float)(k - kbase);
-            const float ur0 = (M * fmaf(-hdl, kf, zb) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
+            const float ur0 = (M * z_rel(a, zb, zb_lo, kf) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
             const float dur = M * a.dz_over_dw;
             if (k > kfull_lo && k < kfull_hi)
                 bp_view<PITCH, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
@@ -437,6 +470,7 @@ static BPArgs bp_args(const Plan &p)
     a.w0 = p.pi_w0;
     a.w1 = p.pi_w1;
     a.trig = p.trig;
+    a.trig_lo = p.trig_lo;
     a.nx = (int)g.nx;
     a.ny = (int)g.ny;
     a.nz = (int)g.nz;
@@ -464,6 +498,12 @@ static BPArgs bp_args(const Plan &p)
     a.h = p.h;
     a.lambda_first = g.lambda_first;
     a.dlam = p.dlam;
+    const double hdl = p.h * p.dlam;
+    a.hdl = (float)hdl;
+    a.hdl_lo = (float)(hdl - (double)a.hdl);
+    const double K = (-0.5 * (double)(g.n_cols - 1) * g.d_alpha + g.alpha_offset) / g.d_alpha;
+    a.K_hi = (float)K;
+    a.K_lo = (float)(K - (double)a.K_hi);
     return a;
 }
 
@@ -591,25 +631,22 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
         }
     }
     const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
-    const float zb = (float)(a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kmin + 0.5) * a.dlam));
-    const float hdl = (float)(a.h * a.dlam);
+    float zb, zb_lo;
+    z_base(a, s0, kmin, &zb, &zb_lo);
     int km = ((kmin % a.vpt) + a.vpt) % a.vpt;
     const int64_t per_view = (int64_t)a.n_rows * a.gcols;
     for (int k = kmin; k <= kmax; ++k) {
-        const float2 cs = __ldg(a.trig + km);
+        float u, v;
+        view_uv(a, __ldg(a.trig + km), __ldg(a.trig_lo + km), x, y, &u, &v);
         km = (km + 1 == a.vpt) ? 0 : km + 1;
-        const float v = a.R - x * cs.x - y * cs.y;
-        const float u = -x * cs.y + y * cs.x;
         const float inv_v = 1.0f / v;
-        const float alpha = atanf(u * inv_v);
-        const float uc = (alpha - a.alpha0) * a.inv_da;
+        int ci;
+        float fc;
+        column_split(a, atanf(u * inv_v) * a.inv_da, &ci, &fc);
         const float M = a.D * rsqrtf(u * u + v * v);
-        const float zr = zb - hdl * (float)(k - kmin);
+        const float zr = z_rel(a, zb, zb_lo, (float)(k - kmin));
         const float ur0 = (M * zr - a.w0row) * a.inv_dw;
         const float dur = M * a.dz_over_dw;
-        const float cf = floorf(uc);
-        const int ci = (int)cf;
-        const float fc = uc - cf;
         float *view = gF + (int64_t)(k - a.first_view) * per_view;
 #pragma unroll
         for (int t = 0; t < BP_T; ++t) {

@@ -44,6 +44,7 @@ struct Plan {
     float *lw = nullptr;    // [n_rows] length-correction weight
     float *cosa = nullptr;  // [n_cols] cos(alpha_c)
     float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
+    float2 *trig_lo = nullptr;  // their rounding residuals: (cos - float(cos), sin - float(sin))
     int *dev_status = nullptr;  // device error word (bounded waits that gave up), 0 = ok
     size_t plan_bytes = 0;
 };

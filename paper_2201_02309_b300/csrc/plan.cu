@@ -427,7 +427,7 @@ static void free_plan(Plan *p)
     if (!p) return;
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
                     p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status,
-                    p->bt_hi, p->bt_lo};
+                    p->bt_hi, p->bt_lo, p->trig_lo};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -457,7 +457,8 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->pi_w0, N * nxy)) || (rc = dalloc(p, &p->pi_w1, N * nxy)) ||
         (rc = dalloc(p, &p->slice_kmin, N)) || (rc = dalloc(p, &p->slice_kmax, N)) ||
         (rc = dalloc(p, &p->hk, 2 * nc - 2)) || (rc = dalloc(p, &p->lw, nr)) || (rc = dalloc(p, &p->cosa, nc)) ||
-        (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->dev_status, 1)) ||
+        (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->trig_lo, g.views_per_turn)) ||
+        (rc = dalloc(p, &p->dev_status, 1)) ||
         (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)))
         return rc;
     KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
@@ -465,7 +466,7 @@ static int build(Plan *p)
     // small 1-D tables in FP64 on the host, stored FP32
     {
         std::vector<float> hk(2 * nc - 2), lw(nr), cosa(nc);
-        std::vector<float2> trig(g.views_per_turn);
+        std::vector<float2> trig(g.views_per_turn), trig_lo(g.views_per_turn);
         for (int64_t n = -(nc - 2); n <= nc - 1; ++n)
             hk[n + nc - 2] = (float)(g.d_alpha / (kPi * sin(((double)n - 0.5) * g.d_alpha)));
         for (int64_t r = 0; r < nr; ++r) {
@@ -475,12 +476,15 @@ static int build(Plan *p)
         for (int64_t c = 0; c < nc; ++c) cosa[c] = (float)cos(G.alpha0 + (double)c * g.d_alpha);
         for (int64_t k = 0; k < g.views_per_turn; ++k) {
             double ph = g.lambda_first + ((double)k + 0.5) * G.dlam + g.lambda0;
-            trig[k] = make_float2((float)cos(ph), (float)sin(ph));
+            const double c = cos(ph), s = sin(ph);
+            trig[k] = make_float2((float)c, (float)s);
+            trig_lo[k] = make_float2((float)(c - (double)(float)c), (float)(s - (double)(float)s));
         }
         KATS_CUDA(cudaMemcpy(p->hk, hk.data(), hk.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->lw, lw.data(), lw.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->cosa, cosa.data(), cosa.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        KATS_CUDA(cudaMemcpy(p->trig_lo, trig_lo.data(), trig_lo.size() * sizeof(float2), cudaMemcpyHostToDevice));
         std::vector<float> bhi((size_t)(p->tc_n * p->tc_k), 0.0f), blo((size_t)(p->tc_n * p->tc_k), 0.0f);
         for (int64_t c = 0; c < nc; ++c)
             for (int64_t cp = 0; cp < p->nc1; ++cp) {

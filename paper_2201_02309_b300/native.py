@@ -20,7 +20,8 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_recon", "katsevich_adjoint", "katsevich_filter", "katsevich_backproject",
            "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
            "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error",
-           "katsevich_recon_noalloc", "katsevich_device_status"]
+           "katsevich_recon_noalloc", "katsevich_device_status", "katsevich_backproject_adjoint",
+           "katsevich_filter_adjoint"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -83,6 +84,8 @@ def load() -> ctypes.CDLL:
         "katsevich_plan_destroy": (None, [P]),
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+        "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
         "katsevich_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -146,6 +149,14 @@ def katsevich_filter(plan, sino_ptr, gF_ptr, batch, precision, ws_ptr, ws_bytes,
 
 def katsevich_backproject(plan, gF_ptr, vol_ptr, batch, stream_ptr) -> None:
     check(load().katsevich_backproject(plan, gF_ptr, vol_ptr, batch, stream_ptr))
+
+
+def katsevich_backproject_adjoint(plan, vol_ptr, gF_ptr, batch, stream_ptr) -> None:
+    check(load().katsevich_backproject_adjoint(plan, vol_ptr, gF_ptr, batch, stream_ptr))
+
+
+def katsevich_filter_adjoint(plan, gF_ptr, sino_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_filter_adjoint(plan, gF_ptr, sino_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr))
 
 
 def katsevich_host_workspace_bytes(plan, batch, precision=KATS_PREC_FP32) -> int:

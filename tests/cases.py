@@ -62,3 +62,13 @@ def narrow_case():
     g = oracle.derive_geometry(cfg)
     sino = np.random.default_rng(8).normal(size=(g["n_views"], g["n_rows"], g["n_cols"]))
     return cfg, g, sino.astype(np.float32)
+
+
+def c3_small_case():
+    """The differentiation scanner (config 3: every 2nd column of the clinical
+    detector, 368 columns, 580 views/turn, 1.5 x max-fit pitch, rows truncated)
+    with a 64 x 64 x 16 volume, so the oracle's transpose stays fast."""
+    cfg = dict(synth.config(3))
+    cfg.update(nx=64, ny=64, nz=16, turns=2)
+    g = oracle.derive_geometry(cfg)
+    return cfg, g
