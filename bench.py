@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32",
+                    help="storage precision of the intermediate data (precision form)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
@@ -249,9 +251,10 @@ def run_ours(args):
     cfg, sino_np = workload(args.config, g, cfg)
     plan = kats.Plan(g)
     info = plan.info
+    prec = {"fp32": kats.KATS_PREC_FP32, "bf16": kats.KATS_PREC_BF16, "fp16": kats.KATS_PREC_FP16}[args.precision]
     sino = torch.from_numpy(sino_np).to(dev)
     vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
-    ws = plan.workspace(device=dev)
+    ws = plan.workspace(precision=prec, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -266,7 +269,7 @@ def run_ours(args):
         return float(t.item())
 
     for _ in range(args.warmup):
-        plan.recon(sino, out=vol, workspace=ws)
+        plan.recon(sino, out=vol, workspace=ws, precision=prec)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -275,7 +278,7 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.recon(sino, out=vol, workspace=ws)
+        plan.recon(sino, out=vol, workspace=ws, precision=prec)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -284,48 +287,51 @@ def run_ours(args):
     ms, value = job_throughput(e0.elapsed_time(e1) / args.steps, info["update_count"], world, max_over_ranks)
     updates = info["update_count"] * world
 
-    # per-kernel durations over the same work (events on the launching stream)
-    gF = torch.empty(plan.filtered_shape, dtype=torch.float32, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        ev[3 * i].record(stream)
-        kats.native.katsevich_filter(plan.handle, sino.data_ptr(), gF.data_ptr(), 1, 0, ws.data_ptr(), ws.numel(),
-                                     stream.cuda_stream)
-        ev[3 * i + 1].record(stream)
-        kats.native.katsevich_backproject(plan.handle, gF.data_ptr(), vol.data_ptr(), 1, stream.cuda_stream)
-        ev[3 * i + 2].record(stream)
-    torch.cuda.synchronize()
-    t_filter = statistics.mean(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps))
-    t_bp = statistics.mean(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps))
+    roofline = None
+    if args.precision == "fp32":
+        # per-kernel durations over the same work (events on the launching stream)
+        gF = torch.empty(plan.filtered_shape, dtype=torch.float32, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            ev[3 * i].record(stream)
+            kats.native.katsevich_filter(plan.handle, sino.data_ptr(), gF.data_ptr(), 1, 0, ws.data_ptr(), ws.numel(),
+                                         stream.cuda_stream)
+            ev[3 * i + 1].record(stream)
+            kats.native.katsevich_backproject(plan.handle, gF.data_ptr(), vol.data_ptr(), 1, stream.cuda_stream)
+            ev[3 * i + 2].record(stream)
+        torch.cuda.synchronize()
+        t_filter = statistics.mean(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps))
+        t_bp = statistics.mean(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps))
 
-    pk, pk_kind = peaks()
-    sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
-    # Backprojection reads 4 fp32 detector taps (16 B) per voxel-view update from the
-    # shared-memory window the TMA stages; its roofline is the SM data path
-    # (148 SMs x 128 B/clk x clock), not HBM.
-    bytes_per_update = 16.0
-    smem_peak = 148 * 128 * sm_mhz * 1e6 / 1e9  # GB/s
-    alg_bytes = info["update_count"] * bytes_per_update
-    achieved = alg_bytes / (t_bp / 1e3) / 1e9
-    roofline = {"kernel": "k_backproject_tma", "bound": "alu", "achieved": achieved, "peak": smem_peak,
-                "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("k_backproject_tma"),
-                "peak_source": f"shared-memory data path: 148 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk_kind} clock)",
-                "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": t_bp, "filter_ms": t_filter}
+        pk, pk_kind = peaks()
+        sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
+        # Backprojection reads 4 fp32 detector taps (16 B) per voxel-view update from the
+        # shared-memory window the TMA stages; its roofline is the SM data path
+        # (148 SMs x 128 B/clk x clock), not HBM.
+        bytes_per_update = 16.0
+        smem_peak = 148 * 128 * sm_mhz * 1e6 / 1e9  # GB/s
+        alg_bytes = info["update_count"] * bytes_per_update
+        achieved = alg_bytes / (t_bp / 1e3) / 1e9
+        roofline = {"kernel": "k_backproject_tma", "bound": "alu", "achieved": achieved, "peak": smem_peak,
+                    "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("k_backproject_tma"),
+                    "peak_source": f"shared-memory data path: 148 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk_kind} clock)",
+                    "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": t_bp, "filter_ms": t_filter}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
         hs = torch.from_numpy(sino_np).pin_memory()
         hv = torch.empty(plan.vol_shape, dtype=torch.float32).pin_memory()
-        wsh = torch.empty(kats.native.katsevich_host_workspace_bytes(plan.handle, 1), dtype=torch.uint8, device=dev)
+        wsh = torch.empty(kats.native.katsevich_host_workspace_bytes(plan.handle, 1, prec), dtype=torch.uint8,
+                          device=dev)
         for _ in range(max(1, args.warmup)):
-            plan.recon_host(hs, hv, workspace=wsh)
+            plan.recon_host(hs, hv, workspace=wsh, precision=prec)
         barrier()
         times = []
         for _ in range(args.steps):
             t = time.perf_counter()
-            plan.recon_host(hs, hv, workspace=wsh)
+            plan.recon_host(hs, hv, workspace=wsh, precision=prec)
             times.append(time.perf_counter() - t)
         te = max_over_ranks(statistics.mean(times))
         h2d = (info["n_filtered_views"] + 1) * g["n_rows"] * g["n_cols"] * 4
@@ -340,8 +346,8 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": describe(cfg, g, info), "vol_per_s": world / (ms / 1e3),
+                "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
+                "data": "synthetic", "config": describe(cfg, g, info, args.precision), "vol_per_s": world / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -61,8 +61,13 @@ extern "C" {
 #define KATS_ETIMEOUT 5 /* a bounded wait gave up                               */
 #define KATS_ESPACE 6   /* caller workspace smaller than required              */
 
-/* Storage precision of the filtered data g^F (the derivative and Hilbert
- * inputs follow it); arithmetic accumulates in FP32 in every mode. */
+/* Storage precision of the intermediate data (precision form of the operator):
+ * FP32 everywhere, or the rebinned derivative data and the filtered data g^F
+ * stored in BF16 / FP16 (scaled by d_alpha), the Hilbert contraction on 16-bit
+ * tensor cores with the Toeplitz operand split hi + lo, interpolation of the
+ * column pair in packed 16-bit arithmetic, and FP32 accumulation.  The reduced
+ * forms are available for katsevich_recon and katsevich_recon_host; every other
+ * entry point takes KATS_PREC_FP32. */
 #define KATS_PREC_FP32 0
 #define KATS_PREC_BF16 1
 #define KATS_PREC_FP16 2
@@ -146,6 +151,8 @@ KATS_API int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision)
 /*
  * Full operator, steps 1-7 (Sec. II reconstruction step), for `batch`
  * sinograms: sino [batch][n_views][n_rows][n_cols] -> vol [batch][nz][ny][nx].
+ * `precision` is one of KATS_PREC_*; the 16-bit forms need the staged
+ * backprojection (KATS_EINVAL for detectors narrower than its column window).
  * Only sinogram views [first_view, first_view + n_filtered_views] are read.
  * `workspace` (device, >= katsevich_workspace_bytes) is scratch owned by the
  * caller; `stream` is a cudaStream_t (NULL = legacy default stream).

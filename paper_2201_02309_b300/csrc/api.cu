@@ -16,7 +16,8 @@ size_t view_elems(const Plan &p) { return (size_t)(p.g.n_rows * p.g.n_cols); }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-int check_common(const kats_plan *plan, const void *in, const void *out, int batch, int precision, const void *ws)
+int check_common(const kats_plan *plan, const void *in, const void *out, int batch, int precision, const void *ws,
+                 bool allow16 = false)
 {
     if (!plan || !in || !out) {
         set_error("null plan or buffer");
@@ -26,8 +27,11 @@ int check_common(const kats_plan *plan, const void *in, const void *out, int bat
         set_error("batch must be >= 1 (got %d)", batch);
         return KATS_EINVAL;
     }
-    if (precision != KATS_PREC_FP32) {
-        set_error("precision %d is not available in this build", precision);
+    const bool is16 = precision == KATS_PREC_BF16 || precision == KATS_PREC_FP16;
+    if (precision != KATS_PREC_FP32 && !(allow16 && is16)) {
+        set_error(is16 ? "reduced precision is available for katsevich_recon / katsevich_recon_host only"
+                       : "unknown precision %d",
+                  precision);
         return KATS_EINVAL;
     }
     if (!ws) {
@@ -46,6 +50,26 @@ int check_common(const kats_plan *plan, const void *in, const void *out, int bat
 }
 
 size_t recon_ws(const Plan &p) { return align256(gf_bytes(p)) + filter_workspace_bytes(p); }
+// reduced precision: row-pair filtered data [n_fviews][n_rows + 1][gf_cols] words + 16-bit filter scratch
+size_t gfp_bytes(const Plan &p) { return 4 * (size_t)(p.n_fviews * (p.g.n_rows + 1) * p.gf_cols); }
+size_t recon16_ws(const Plan &p) { return align256(gfp_bytes(p)) + filter16_workspace_bytes(p); }
+size_t recon_ws_for(const Plan &p, int precision) { return precision == KATS_PREC_FP32 ? recon_ws(p) : recon16_ws(p); }
+
+// One item of steps 1-7 with the workspace layout of the given precision.
+int recon_item(const Plan &p, int precision, const float *sino_first, float *vol, void *ws, size_t ws_bytes,
+               cudaStream_t st)
+{
+    if (precision == KATS_PREC_FP32) {
+        float *gF = (float *)ws;
+        char *fws = (char *)ws + align256(gf_bytes(p));
+        int rc = launch_filter(p, sino_first, gF, fws, ws_bytes - align256(gf_bytes(p)), st);
+        return rc ? rc : launch_backproject(p, gF, vol, st);
+    }
+    uint32_t *gFp = (uint32_t *)ws;
+    char *fws = (char *)ws + align256(gfp_bytes(p));
+    int rc = launch_filter16(p, precision, sino_first, gFp, fws, ws_bytes - align256(gfp_bytes(p)), st);
+    return rc ? rc : launch_backproject16(p, precision, gFp, vol, st);
+}
 size_t adjoint_ws(const Plan &p) { return align256(gf_bytes(p)) + filter_adjoint_workspace_bytes(p); }
 
 }  // namespace
@@ -54,9 +78,11 @@ extern "C" {
 
 int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision)
 {
-    if (!plan || precision != KATS_PREC_FP32) return -1;
+    if (!plan) return -1;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
-    return (int64_t)std::max(recon_ws(p), adjoint_ws(p));
+    if (precision == KATS_PREC_FP32) return (int64_t)std::max(recon_ws(p), adjoint_ws(p));
+    if (precision == KATS_PREC_BF16 || precision == KATS_PREC_FP16) return (int64_t)recon16_ws(p);
+    return -1;
 }
 
 int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int batch, int precision, void *workspace,
@@ -96,21 +122,18 @@ int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, in
 int katsevich_recon(const kats_plan *plan, const float *sino, float *vol, int batch, int precision, void *workspace,
                     size_t workspace_bytes, void *stream)
 {
-    int rc = check_common(plan, sino, vol, batch, precision, workspace);
+    int rc = check_common(plan, sino, vol, batch, precision, workspace, true);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
-    if (workspace_bytes < recon_ws(p)) {
-        set_error("workspace %zu < %zu bytes", workspace_bytes, recon_ws(p));
+    const size_t need = recon_ws_for(p, precision);
+    if (workspace_bytes < need) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, need);
         return KATS_ESPACE;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    float *gF = (float *)workspace;
-    char *fws = (char *)workspace + align256(gf_bytes(p));
-    const size_t fws_bytes = workspace_bytes - align256(gf_bytes(p));
     for (int b = 0; b < batch; ++b) {
-        rc = launch_filter(p, sino + b * sino_item(p) + p.first_view * view_elems(p), gF, fws, fws_bytes, st);
-        if (rc) return rc;
-        rc = launch_backproject(p, gF, vol + b * vol_item(p), st);
+        rc = recon_item(p, precision, sino + b * sino_item(p) + p.first_view * view_elems(p), vol + b * vol_item(p),
+                        workspace, workspace_bytes, st);
         if (rc) return rc;
     }
     return KATS_OK;
@@ -174,16 +197,18 @@ int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, float *sino
 
 int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision)
 {
-    if (!plan || batch < 1 || precision != KATS_PREC_FP32) return -1;
+    if (!plan || batch < 1 || (precision != KATS_PREC_FP32 && precision != KATS_PREC_BF16 &&
+                               precision != KATS_PREC_FP16))
+        return -1;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
     const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
-    return (int64_t)(align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws(p));
+    return (int64_t)(align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws_for(p, precision));
 }
 
 int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch, int precision,
                          void *workspace, size_t workspace_bytes, void *stream)
 {
-    int rc = check_common(plan, host_sino, host_vol, batch, precision, workspace);
+    int rc = check_common(plan, host_sino, host_vol, batch, precision, workspace, true);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
     const int64_t need = katsevich_host_workspace_bytes(plan, batch, precision);
@@ -196,16 +221,11 @@ int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *h
     float *d_win = (float *)workspace;
     float *d_vol = (float *)((char *)workspace + align256(win));
     char *rws = (char *)d_vol + align256(sizeof(float) * vol_item(p));
-    const size_t rws_bytes = recon_ws(p);
-    float *gF = (float *)rws;
-    char *fws = rws + align256(gf_bytes(p));
-    const size_t fws_bytes = rws_bytes - align256(gf_bytes(p));
+    const size_t rws_bytes = recon_ws_for(p, precision);
     for (int b = 0; b < batch; ++b) {
         KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + b * sino_item(p) + p.first_view * view_elems(p), win,
                                   cudaMemcpyHostToDevice, st));
-        rc = launch_filter(p, d_win, gF, fws, fws_bytes, st);
-        if (rc) return rc;
-        rc = launch_backproject(p, gF, d_vol, st);
+        rc = recon_item(p, precision, d_win, d_vol, rws, rws_bytes, st);
         if (rc) return rc;
         KATS_CUDA(cudaMemcpyAsync(host_vol + b * vol_item(p), d_vol, sizeof(float) * vol_item(p),
                                   cudaMemcpyDeviceToHost, st));

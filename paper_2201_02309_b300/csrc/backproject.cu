@@ -17,6 +17,8 @@
 // k_backproject (fallback for windows TMA cannot stage): the same arithmetic
 // with bounds-tested loads from global memory.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -180,6 +182,7 @@ struct BP2Args {
     int srows;        // staged rows: n_rows + 3 (row 0 and rows n_rows+1.. are zero fill)
     int slot_floats;  // floats per staged view, multiple of 32 (128-byte slots)
     int *status;
+    float out_scale;  // dl / 2pi, divided by d_alpha for the scaled 16-bit storage
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -244,35 +247,112 @@ __device__ __forceinline__ float angle_cols(const BPArgs &a, float t)
     return atanf(t) * a.inv_da;
 }
 
-// One view's contribution to a thread's B2_T slices, reading taps from
-// smem[colx + (row << log2 PITCH)] (colx carries the -2^23 row-bias of the
-// floor trick, in modulo-2^32 arithmetic).  WEIGHTED: the view ends some
-// slice's PI window (end weights, or zero outside it); otherwise every slice
-// takes it with weight 1.  CLAMP: keep the row inside the staged window
-// (needed whenever a slice can be outside its PI window or the plan cannot
-// prove rows stay within one row of the detector).
-template <int PITCH, bool WEIGHTED, bool CLAMP>
-__device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
-                                        float inv_v, float kf, const float *lo, const float *hi, float *acc)
+// One tap of one slice: bilinear sample at (column colx + fc, row ur) of the
+// staged window, smem[colx + (row << log2 PITCH)] (colx carries the -2^23
+// row-bias of the floor trick, in modulo-2^32 arithmetic), accumulated with
+// weight w.  CLAMP keeps the row inside the staged window (needed whenever
+// the plan cannot prove rows stay within one row of the detector).
+template <int PITCH, int MODE, bool CLAMP>
+__device__ __forceinline__ void bp_tap(const float *smem, uint32_t colx, float fc, __half2 fch, float ur, float rmax,
+                                       float w, float &acc)
 {
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
+    if (CLAMP) ur = fminf(fmaxf(ur, 0.0f), rmax);
+    const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur), ur >= 0
+    const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
+    const float fr = ur - (yv - 8388608.0f);
+    float top, bot;
+    if (MODE == 0) {
+        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + PITCH], v11 = smem[q + PITCH + 1];
+        top = fmaf(fc, v01 - v00, v00);
+        bot = fmaf(fc, v11 - v10, v10);
+    } else if (MODE == 2) {
+        // each staged word holds the row pair (g[r-1][c], g[r][c]); fp16 interpolates
+        // the column pair in packed half2 arithmetic
+        const __half2 a = reinterpret_cast<const __half2 *>(smem)[q];
+        const __half2 b = reinterpret_cast<const __half2 *>(smem)[q + 1];
+        const __half2 m = __hfma2(fch, __hsub2(b, a), a);
+        top = __low2float(m);
+        bot = __high2float(m);
+    } else {
+        // bf16 keeps 8 fraction bits: interpolate in FP32 after the (exact) unpacking
+        const float2 a = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(smem)[q]);
+        const float2 b = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(smem)[q + 1]);
+        top = fmaf(fc, b.x - a.x, a.x);
+        bot = fmaf(fc, b.y - a.y, a.y);
+    }
+    acc = fmaf(w, fmaf(fr, bot - top, top), acc);
+}
+
+// Two slices' taps (rows ur2.x, ur2.y, same column) in packed FP32x2
+// arithmetic: every component is rounded exactly as the scalar tap rounds it
+// (a - b is formed as fma(b, -1, a)), at half the instruction count.
+template <int PITCH, bool CLAMP>
+__device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2 fc2, float2 ur2, float rmax,
+                                        float2 w2, float2 &acc2)
+{
+    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
+    if (CLAMP) {
+        ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
+        ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
+    }
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 yv = __fadd2_rd(ur2, make_float2(8388608.0f, 8388608.0f));  // 2^23 + floor(ur)
+    const uint32_t q0 = colx + ((uint32_t)__float_as_int(yv.x) << SH);
+    const uint32_t q1 = colx + ((uint32_t)__float_as_int(yv.y) << SH);
+    const float2 fr = __ffma2_rn(__fadd2_rn(yv, make_float2(-8388608.0f, -8388608.0f)), m1, ur2);
+    const float2 v00 = make_float2(smem[q0], smem[q1]);
+    const float2 v01 = make_float2(smem[q0 + 1], smem[q1 + 1]);
+    const float2 v10 = make_float2(smem[q0 + PITCH], smem[q1 + PITCH]);
+    const float2 v11 = make_float2(smem[q0 + PITCH + 1], smem[q1 + PITCH + 1]);
+    const float2 top = __ffma2_rn(fc2, __ffma2_rn(v00, m1, v01), v00);
+    const float2 bot = __ffma2_rn(fc2, __ffma2_rn(v10, m1, v11), v10);
+    acc2 = __ffma2_rn(w2, __ffma2_rn(fr, __ffma2_rn(top, m1, bot), top), acc2);
+}
+
+// One view's contribution to a thread's B2_T slices (accumulators in pairs).
+// WEIGHTED: the view ends some slice's PI window (end weights; slices outside
+// their window are skipped).  FP32 data runs slice pairs in FP32x2; a pair
+// with one slice outside its window still loads that slice's taps (weight
+// zero), so weighted pairs always clamp.  The scalar 16-bit forms skip such
+// slices, so every tap they take lies in a PI window and CLAMP follows the
+// plan's row proof; otherwise every slice takes the view with weight 1.
+template <int PITCH, int MODE, bool WEIGHTED, bool CLAMP>
+__device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
+                                        float inv_v, float kf, const float *lo, const float *hi, float2 *acc2)
+{
+    if (MODE == 0 && !WEIGHTED) {
+        const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
+        const float2 w2 = make_float2(inv_v, inv_v);
+#pragma unroll
+        for (int pr = 0; pr < B2_T / 2; ++pr)
+            bp_tap2<PITCH, CLAMP>(smem, colx, fc2, __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02), rmax, w2,
+                                  acc2[pr]);
+        return;
+    }
+    if (MODE == 0 && WEIGHTED) {
+        const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
+#pragma unroll
+        for (int pr = 0; pr < B2_T / 2; ++pr) {
+            const float om0 = __saturatef(kf - lo[2 * pr]) * __saturatef(hi[2 * pr] - kf);
+            const float om1 = __saturatef(kf - lo[2 * pr + 1]) * __saturatef(hi[2 * pr + 1] - kf);
+            if (om0 == 0.0f && om1 == 0.0f) continue;
+            bp_tap2<PITCH, true>(smem, colx, fc2, __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02), rmax,
+                                 make_float2(om0 * inv_v, om1 * inv_v), acc2[pr]);
+        }
+        return;
+    }
+    const __half2 fch = __float2half2_rn(fc);
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
-        float om = 1.0f;
+        float w = inv_v;
         if (WEIGHTED) {
-            om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
+            const float om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
             if (om == 0.0f) continue;
+            w = om * inv_v;
         }
-        float ur = fmaf((float)t, dur, ur0);
-        if (CLAMP) ur = fminf(fmaxf(ur, 0.0f), rmax);
-        const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur), ur >= 0
-        const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
-        const float fr = ur - (yv - 8388608.0f);
-        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + PITCH], v11 = smem[q + PITCH + 1];
-        const float top = fmaf(fc, v01 - v00, v00);
-        const float bot = fmaf(fc, v11 - v10, v10);
-        const float val = fmaf(fr, bot - top, top);
-        acc[t] = fmaf(WEIGHTED ? om * inv_v : inv_v, val, acc[t]);
+        bp_tap<PITCH, MODE, CLAMP>(smem, colx, fc, fch, fmaf((float)t, dur, ur0), rmax, w,
+                                   (t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x);
     }
 }
 
@@ -283,7 +363,7 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-template <int PITCH, bool POLY, bool ROWS_OK>
+template <int PITCH, int MODE, bool POLY, bool ROWS_OK>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
@@ -305,7 +385,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 
     // per-slice view windows; weights omega(k) = sat(k - lo_t) * sat(hi_t - k) relative to kbase
     int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
-    float lo[B2_T], hi[B2_T], acc[B2_T];
+    float lo[B2_T], hi[B2_T];
+    float2 acc2[B2_T / 2];
     {
         int ka[B2_T], kb[B2_T];
         float wa[B2_T], wb[B2_T];
@@ -330,8 +411,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         }
         const int kbase = active ? kmin : 0;
 #pragma unroll
+        for (int t = 0; t < B2_T / 2; ++t) acc2[t] = make_float2(0.0f, 0.0f);
+#pragma unroll
         for (int t = 0; t < B2_T; ++t) {
-            acc[t] = 0.0f;
             if (ka[t] <= kb[t]) {
                 lo[t] = (float)(ka[t] - kbase) - wa[t];
                 hi[t] = (float)(kb[t] - kbase) + wb[t];
@@ -391,7 +473,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 s_col[slot] = clo;
                 s_cs[slot] = cs;
                 mbar_arrive_expect_tx(&s_full[slot], box_bytes);
-                tma_load_3d(dst0 + 4u * (uint32_t)(slot * p.slot_floats), &gmap, &s_full[slot], clo, -1,
+                // fp32 windows start one zero row above the detector; row-pair windows at pair-row 0
+                tma_load_3d(dst0 + 4u * (uint32_t)(slot * p.slot_floats), &gmap, &s_full[slot], clo, MODE == 0 ? -1 : 0,
                             K0 + j - (int)a.first_view);
             }
             __syncwarp();
@@ -441,9 +524,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             const float ur0 = (M * z_rel(a, zb, zb_lo, kf) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
             const float dur = M * a.dz_over_dw;
             if (k > kfull_lo && k < kfull_hi)
-                bp_view<PITCH, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
             else
-                bp_view<PITCH, true, true>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc);
+                bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[slot]);
@@ -456,7 +539,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
         const int s = s0 + t;
-        if (s < a.nz) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = acc[t] * a.scale;
+        if (s < a.nz) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = ((t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x) * p.out_scale;
     }
 }
 
@@ -540,40 +623,70 @@ static int window_cols(const Plan &p)
     return ((int)ceil(span) + 8 + 3) / 4 * 4;
 }
 
-template <int PITCH>
-static int launch_tma(const Plan &p, const BPArgs &a, const float *gF, int W, cudaStream_t st, bool *launched)
+template <int PITCH, int MODE>
+static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched)
 {
     *launched = false;
-    const int srows = (int)p.g.n_rows + 3;
+    // staged rows: fp32 -> detector rows -1 .. n_rows + 1; row pairs -> pair-rows 0 .. n_rows + 1
+    const int srows = (int)p.g.n_rows + (MODE == 0 ? 3 : 2);
     const int slot = (PITCH * srows + 31) / 32 * 32;
     const size_t smem = sizeof(float) * (size_t)slot * B2_R + 128;  // + base alignment slack
     EncodeTiledFn enc = encode_fn();
     if (!enc || W > PITCH || PITCH > p.gf_cols || srows > 256 || smem > 200 * 1024 ||
         (reinterpret_cast<uintptr_t>(gF) % 16) != 0 || p.n_fviews >= INT32_MAX)
         return KATS_OK;
+    const int64_t drows = p.g.n_rows + (MODE == 0 ? 0 : 1);
     CUtensorMap map;
-    cuuint64_t dims[3] = {(cuuint64_t)p.gf_cols, (cuuint64_t)p.g.n_rows, (cuuint64_t)p.n_fviews};
-    cuuint64_t strides[2] = {(cuuint64_t)p.gf_cols * 4, (cuuint64_t)(p.gf_cols * p.g.n_rows) * 4};
+    cuuint64_t dims[3] = {(cuuint64_t)p.gf_cols, (cuuint64_t)drows, (cuuint64_t)p.n_fviews};
+    cuuint64_t strides[2] = {(cuuint64_t)p.gf_cols * 4, (cuuint64_t)(p.gf_cols * drows) * 4};
     cuuint32_t box[3] = {(cuuint32_t)PITCH, (cuuint32_t)srows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)gF, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return KATS_OK;
-    BP2Args b{a, W, srows, slot, p.dev_status};
+    BP2Args b{a, W, srows, slot, p.dev_status, (float)(p.dlam / (2.0 * kPi) / (MODE == 0 ? 1.0 : p.g.d_alpha))};
     // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
     const bool poly = p.r_fov <= p.g.R * 0.70710678;
     // every contributing row within half a row of the detector (plan extents, FP32 on device)
     const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
     const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
-    auto kern = poly ? (rows_ok ? k_backproject_tma<PITCH, true, true> : k_backproject_tma<PITCH, true, false>)
-                     : (rows_ok ? k_backproject_tma<PITCH, false, true> : k_backproject_tma<PITCH, false, false>);
+    auto kern = poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true> : k_backproject_tma<PITCH, MODE, true, false>)
+                     : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true> : k_backproject_tma<PITCH, MODE, false, false>);
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY), (unsigned)ceil_div(p.g.nz, B2_T));
     kern<<<grid, B2_THREADS, smem, st>>>(map, b);
     KATS_CUDA(cudaGetLastError());
     *launched = true;
+    return KATS_OK;
+}
+
+template <int MODE>
+static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched)
+{
+    if (W <= 32) return launch_tma<32, MODE>(p, a, gF, W, st, launched);
+    if (W <= 64) return launch_tma<64, MODE>(p, a, gF, W, st, launched);
+    if (W <= 128) return launch_tma<128, MODE>(p, a, gF, W, st, launched);
+    *launched = false;
+    return KATS_OK;
+}
+
+int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st)
+{
+    BPArgs a = bp_args(p);
+    a.gF = nullptr;
+    a.vol = vol;
+    bool launched = false;
+    const int W = window_cols(p);
+    int rc = prec == KATS_PREC_FP16 ? launch_tma_any<2>(p, a, gFp, W, st, &launched)
+                                    : launch_tma_any<1>(p, a, gFp, W, st, &launched);
+    if (rc) return rc;
+    if (!launched) {
+        set_error("reduced-precision backprojection needs the staged (TMA) kernel; this detector is narrower than "
+                  "its column window");
+        return KATS_EINVAL;
+    }
     return KATS_OK;
 }
 
@@ -584,10 +697,7 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
     a.vol = vol;
     const int W = window_cols(p);
     bool launched = false;
-    int rc = KATS_OK;
-    if (W <= 32) rc = launch_tma<32>(p, a, gF, W, st, &launched);
-    else if (W <= 64) rc = launch_tma<64>(p, a, gF, W, st, &launched);
-    else if (W <= 128) rc = launch_tma<128>(p, a, gF, W, st, &launched);
+    int rc = launch_tma_any<0>(p, a, gF, W, st, &launched);
     if (rc || launched) return rc;
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
     k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);

@@ -41,6 +41,10 @@ struct Plan {
     // (exact in TF32) and lo = value - hi; [tc_n][tc_k] row-major.
     float *bt_hi = nullptr, *bt_lo = nullptr;
     int64_t tc_k = 0, tc_n = 0;  // K padded to 32, N padded to 256
+    // the same operand for the 16-bit Hilbert step: value = hi + lo with hi, lo
+    // in bf16 (resp. fp16), [tc_n][tc_k16], K padded to 64
+    uint16_t *bt16_hi[2] = {nullptr, nullptr}, *bt16_lo[2] = {nullptr, nullptr};  // [0] bf16, [1] fp16
+    int64_t tc_k16 = 0;
     float *lw = nullptr;    // [n_rows] length-correction weight
     float *cosa = nullptr;  // [n_cols] cos(alpha_c)
     float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
@@ -65,6 +69,17 @@ int cuda_fail(cudaError_t e, const char *what);
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Kernel launchers (defined in filter.cu, backproject.cu, adjoint.cu).
+// Reduced-precision storage (KATS_PREC_BF16 / KATS_PREC_FP16): derivative data
+// and filtered data are stored as 16-bit values scaled by d_alpha; the
+// filtered data use a row-pair layout, one 32-bit word (g[r-1][c], g[r][c])
+// per pair-row r = 0..n_rows ([n_fviews][n_rows + 1][gf_cols] words).
+size_t filter16_workspace_bytes(const Plan &p);
+int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
+                    cudaStream_t st);
+int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st);
+int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, int64_t M, int ldc, cudaStream_t st,
+                        bool *done);
+
 // sino points at sinogram view p.first_view; gF receives p.n_fviews filtered views
 int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st);
 // gF: [p.n_fviews][n_rows][p.gf_cols], view 0 = half-view p.first_view, pad columns zero

@@ -319,7 +319,186 @@ bool encode_2d(EncodeFn enc, CUtensorMap *map, const float *ptr, int64_t inner, 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------- 16-bit A
+// kind::f16 variant for reduced-precision storage: A (g3 * d_alpha) is exact
+// in bf16 / fp16, the Toeplitz operand is split hi + lo in the same type, and
+//     C = A T_hi + A T_lo
+// accumulates in FP32 in TMEM.  Warps: 0 TMA producer, 1 MMA issuer, 2..5
+// epilogue; K blocks of 64 elements (one 128-byte swizzle span).
+constexpr int T16_K = 64;
+constexpr uint32_t T16_A_BYTES = TC_M * T16_K * 2;  // 16 KB
+constexpr uint32_t T16_B_BYTES = TC_N * T16_K * 2;  // 32 KB
+constexpr uint32_t T16_STAGE_BYTES = T16_A_BYTES + 2 * T16_B_BYTES;
+constexpr uint32_t T16_SMEM = TC_STAGES * T16_STAGE_BYTES + 1024;
+
+// kind::f16 descriptor: D fp32, A and B bf16 (format 1) or fp16 (format 0), K-major.
+template <bool FP16>
+__device__ __forceinline__ uint32_t idesc_f16()
+{
+    const uint32_t f = FP16 ? 0u : 1u;
+    return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+template <bool FP16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_hilbert_tc16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
+                   const __grid_constant__ CUtensorMap mapBl, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t s_full[TC_STAGES], s_empty[TC_STAGES], s_acc;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_issued;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (saddr(tc_raw) + 1023u) & ~1023u;
+    const int64_t m0 = (int64_t)blockIdx.y * TC_M;
+    const int n0 = blockIdx.x * TC_N;
+    auto stA = [&](int s) { return base + (uint32_t)s * T16_STAGE_BYTES; };
+    auto stBh = [&](int s) { return stA(s) + T16_A_BYTES; };
+    auto stBl = [&](int s) { return stA(s) + T16_A_BYTES + T16_B_BYTES; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            bar_init(&s_full[s], 1);
+            bar_init(&s_empty[s], 1);
+        }
+        bar_init(&s_acc, 1);
+        s_abort = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                     "r"((uint32_t)TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    const int nkb = a.kblocks;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (kb >= TC_STAGES && !bar_wait(&s_empty[s], (uint32_t)(((kb >> 1) - 1) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                bar_expect(&s_full[s], T16_A_BYTES + 2 * T16_B_BYTES);
+                tma_2d(stA(s), &mapA, &s_full[s], kb * T16_K, (int)m0);
+                tma_2d(stBh(s), &mapBh, &s_full[s], kb * T16_K, n0);
+                tma_2d(stBl(s), &mapBl, &s_full[s], kb * T16_K, n0);
+                s_issued = kb + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16<FP16>();
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1;
+                if (!bar_wait(&s_full[s], (uint32_t)((kb >> 1) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                fence_after();
+#pragma unroll
+                for (int kk = 0; kk < T16_K / 16; ++kk) {  // 16 elements = 32 bytes per MMA
+                    const uint32_t off = (uint32_t)kk * 32u;
+                    const uint64_t dA = sw128_desc(stA(s) + off);
+                    mma_f16(tmem, dA, sw128_desc(stBh(s) + off), idesc, (kb | kk) != 0);
+                    mma_f16(tmem, dA, sw128_desc(stBl(s) + off), idesc, 1u);
+                }
+                mma_commit(&s_empty[s]);
+            }
+            mma_commit(&s_acc);
+        }
+    } else {
+        const bool done = bar_wait(&s_acc, 0u);
+        if (!done) atomicExch(&s_abort, 1);
+        fence_after();
+        if (done && !*(volatile int *)&s_abort) {
+            const int quarter = warp & 3;
+            const int64_t row = m0 + quarter * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+            for (int cb = 0; cb < TC_N / 32; ++cb) {
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)(cb * 32), v);
+                if (row < a.M) {
+                    float4 *out = reinterpret_cast<float4 *>(a.C + row * a.ldc + n0 + cb * 32);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        for (int kb = max(0, s_issued - TC_STAGES); kb < s_issued; ++kb)
+            bar_wait(&s_full[kb & 1], (uint32_t)((kb >> 1) & 1));
+        atomicExch(a.status, kDevStatusTimeout);
+    }
+    if (warp == 1) {
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_N)
+                     : "memory");
+    }
+}
+
+bool encode_2d_u16(EncodeFn enc, CUtensorMap *map, const uint16_t *ptr, int64_t inner, int64_t outer, int box_inner,
+                   int box_outer)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+// g4[M][ldc] = (g3 * d_alpha)[M][tc_k16] . T, 16-bit operands, fp32 accumulation.
+int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, int64_t M, int ldc, cudaStream_t st,
+                        bool *done)
+{
+    *done = false;
+    EncodeFn enc = encoder();
+    const int kind = prec == KATS_PREC_FP16 ? 1 : 0;
+    if (!enc || M < 1 || ldc % TC_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(g4) % 16) != 0 || ceil_div(M, TC_M) > 65535)
+        return KATS_OK;
+    CUtensorMap mA, mBh, mBl;
+    if (!encode_2d_u16(enc, &mA, g3, p.tc_k16, M, T16_K, TC_M) ||
+        !encode_2d_u16(enc, &mBh, p.bt16_hi[kind], p.tc_k16, p.tc_n, T16_K, TC_N) ||
+        !encode_2d_u16(enc, &mBl, p.bt16_lo[kind], p.tc_k16, p.tc_n, T16_K, TC_N))
+        return KATS_OK;
+    TcArgs a{g4, M, ldc, (int)(p.tc_k16 / T16_K), p.dev_status};
+    auto kern = kind ? k_hilbert_tc16<true> : k_hilbert_tc16<false>;
+    KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T16_SMEM));
+    dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
+    kern<<<grid, TC_THREADS, T16_SMEM, st>>>(mA, mBh, mBl, a);
+    KATS_CUDA(cudaGetLastError());
+    *done = true;
+    return KATS_OK;
+}
 
 // g4[M][ldc] = g3[M][tc_k] . T on the tensor cores (ldc a multiple of 256).
 // Returns KATS_OK with *done = false when the tensor-core path cannot run

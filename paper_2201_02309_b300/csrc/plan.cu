@@ -26,6 +26,55 @@ int cuda_fail(cudaError_t e, const char *what)
     return (e == cudaErrorMemoryAllocation) ? KATS_ENOMEM : KATS_ECUDA;
 }
 
+// ------------------------------------------------- host 16-bit conversions
+// Round-to-nearest-even conversions of a double to bfloat16 (8-bit exponent,
+// 7-bit fraction) and IEEE binary16 (5-bit exponent, 10-bit fraction) bit
+// patterns, from the formats' definitions; finite inputs in range only.
+static uint16_t host_to_bf16(double v)
+{
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)((u + rounding) >> 16);
+}
+
+static double host_from_bf16(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+static uint16_t host_to_fp16(double v)
+{
+    const double a = fabs(v);
+    uint16_t sign = v < 0 ? 0x8000 : 0;
+    if (a < 6.103515625e-05) {  // subnormal range: multiples of 2^-24
+        const double q = nearbyint(a * 16777216.0);
+        return (uint16_t)(sign | (uint16_t)q);
+    }
+    int e;
+    const double m = frexp(a, &e);  // a = m 2^e, m in [0.5, 1)
+    double frac = nearbyint((m * 2.0 - 1.0) * 1024.0);
+    int exp = e - 1;
+    if (frac >= 1024.0) {
+        frac = 0.0;
+        exp += 1;
+    }
+    return (uint16_t)(sign | (uint16_t)((exp + 15) << 10) | (uint16_t)frac);
+}
+
+static double host_from_fp16(uint16_t h)
+{
+    const int exp = (h >> 10) & 0x1F;
+    const int frac = h & 0x3FF;
+    const double s = (h & 0x8000) ? -1.0 : 1.0;
+    if (exp == 0) return s * ldexp((double)frac, -24);
+    return s * ldexp(1.0 + frac / 1024.0, exp - 15);
+}
+
 // ----------------------------------------------------------------- geometry
 struct DevGeom {
     double R, D, P, lambda0, z0, lambda_first, dlam, h;
@@ -427,7 +476,8 @@ static void free_plan(Plan *p)
     if (!p) return;
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
                     p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status,
-                    p->bt_hi, p->bt_lo, p->trig_lo};
+                    p->bt_hi, p->bt_lo, p->trig_lo, p->bt16_hi[0], p->bt16_lo[0], p->bt16_hi[1],
+                    p->bt16_lo[1]};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -459,7 +509,9 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->hk, 2 * nc - 2)) || (rc = dalloc(p, &p->lw, nr)) || (rc = dalloc(p, &p->cosa, nc)) ||
         (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->trig_lo, g.views_per_turn)) ||
         (rc = dalloc(p, &p->dev_status, 1)) ||
-        (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)))
+        (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)) ||
+        (rc = dalloc(p, &p->bt16_hi[0], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[0], p->tc_n * p->tc_k16)) ||
+        (rc = dalloc(p, &p->bt16_hi[1], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[1], p->tc_n * p->tc_k16)))
         return rc;
     KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
 
@@ -499,6 +551,29 @@ static int build(Plan *p)
             }
         KATS_CUDA(cudaMemcpy(p->bt_hi, bhi.data(), bhi.size() * sizeof(float), cudaMemcpyHostToDevice));
         KATS_CUDA(cudaMemcpy(p->bt_lo, blo.data(), blo.size() * sizeof(float), cudaMemcpyHostToDevice));
+        // 16-bit pairs: hi = value rounded to the type, lo = remainder rounded to the type
+        const size_t n16 = (size_t)(p->tc_n * p->tc_k16);
+        std::vector<uint16_t> h16(n16, 0), l16(n16, 0);
+        for (int kind = 0; kind < 2; ++kind) {
+            std::fill(h16.begin(), h16.end(), 0);
+            std::fill(l16.begin(), l16.end(), 0);
+            for (int64_t c = 0; c < nc; ++c)
+                for (int64_t cp = 0; cp < p->nc1; ++cp) {
+                    const double v = g.d_alpha / (kPi * sin(((double)(c - cp) - 0.5) * g.d_alpha));
+                    const size_t o = (size_t)(c * p->tc_k16 + cp);
+                    if (kind == 0) {
+                        const uint16_t hb = host_to_bf16(v);
+                        h16[o] = hb;
+                        l16[o] = host_to_bf16(v - host_from_bf16(hb));
+                    } else {
+                        const uint16_t hb = host_to_fp16(v);
+                        h16[o] = hb;
+                        l16[o] = host_to_fp16(v - host_from_fp16(hb));
+                    }
+                }
+            KATS_CUDA(cudaMemcpy(p->bt16_hi[kind], h16.data(), n16 * 2, cudaMemcpyHostToDevice));
+            KATS_CUDA(cudaMemcpy(p->bt16_lo[kind], l16.data(), n16 * 2, cudaMemcpyHostToDevice));
+        }
     }
 
     k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256>>>(G, p->kap_idx, p->kap_frac);
@@ -640,6 +715,7 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->gf_cols = (g->n_cols + 3) / 4 * 4;
     p->tc_k = (p->nc1 + 31) / 32 * 32;
     p->tc_n = (g->n_cols + 255) / 256 * 256;
+    p->tc_k16 = (p->nc1 + 63) / 64 * 64;
     rc = build(p);
     if (rc) {
         free_plan(p);
