@@ -363,6 +363,50 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// Geometry of two consecutive views for one voxel column, in FP32x2 with the
+// scalar path's rounding order: column index and fraction of alpha* (the
+// floor taken as 1.5 * 2^23 + floor(c) rounded down), first staged row of
+// slice 0, row step per slice, and 1/v*.
+struct ViewGeo2 {
+    float2 fc, ur0, dur, inv_v;
+    int ci0, ci1;
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+template <bool POLY>
+__device__ __forceinline__ void view_geo2(const BPArgs &a, float x, float y, float2 csA, float2 csB, float zb,
+                                          float zb_lo, float kfA, ViewGeo2 &g)
+{
+    const float2 m1 = f2(-1.0f);
+    const float2 cx = make_float2(csA.x, csB.x), cy = make_float2(csA.y, csB.y);
+    const float2 v = __ffma2_rn(f2(-x), cx, __ffma2_rn(f2(-y), cy, f2(a.R)));
+    const float2 u = __ffma2_rn(f2(-x), cy, __fmul2_rn(f2(y), cx));
+    g.inv_v = make_float2(rcp_approx(v.x), rcp_approx(v.y));
+    const float2 t = __fmul2_rn(u, g.inv_v);
+    float2 ang;
+    if (POLY) {
+        const float2 s2 = __fmul2_rn(t, t);
+        float2 pp = f2(c_atan[0]);
+#pragma unroll
+        for (int i = 1; i < kAtanTerms; ++i) pp = __ffma2_rn(pp, s2, f2(c_atan[i]));
+        ang = __fmul2_rn(__fmul2_rn(t, pp), f2(a.inv_da));
+    } else {
+        ang = make_float2(atanf(t.x) * a.inv_da, atanf(t.y) * a.inv_da);
+    }
+    const float2 c = __fadd2_rn(__fadd2_rn(ang, f2(-a.K_hi)), f2(-a.K_lo));
+    const float2 yv = __fadd2_rd(c, f2(12582912.0f));  // 1.5 * 2^23 + floor(c), |c| < 2^22
+    g.ci0 = __float_as_int(yv.x) - 0x4B400000;
+    g.ci1 = __float_as_int(yv.y) - 0x4B400000;
+    const float2 cf = __fadd2_rn(yv, f2(-12582912.0f));
+    g.fc = __fadd2_rn(__ffma2_rn(__fadd2_rn(cf, f2(a.K_hi)), m1, ang), f2(-a.K_lo));
+    const float2 M = __fmul2_rn(f2(a.D), make_float2(rsqrtf(fmaf(u.x, u.x, v.x * v.x)), rsqrtf(fmaf(u.y, u.y, v.y * v.y))));
+    const float2 kf = make_float2(kfA, kfA + 1.0f);
+    const float2 zr = __fadd2_rn(__ffma2_rn(f2(-a.hdl), kf, f2(zb)), __ffma2_rn(f2(-a.hdl_lo), kf, f2(zb_lo)));
+    g.ur0 = __ffma2_rn(__ffma2_rn(M, zr, f2(-a.w0row)), f2(a.inv_dw), f2(1.0f));  // staged row 0 = detector row -1
+    g.dur = __fmul2_rn(M, f2(a.dz_over_dw));
+}
+
 template <int PITCH, int MODE, bool POLY, bool ROWS_OK>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
@@ -494,42 +538,61 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         return;
     }
 
-    // ---------------- consumer warps
+    // ---------------- consumer warps: two views per iteration, their per-view
+    // geometry computed together in FP32x2
     const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
     const int kbase = active ? kmin : 0;
     float zb, zb_lo;
     z_base(a, s0, kbase, &zb, &zb_lo);
     const float rmax = (float)(a.n_rows + 1);
+    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
     int slot = 0;
     uint32_t phase = 0;
-    for (int j = 0; j < nviews; ++j) {
-        const int k = K0 + j;
-        if (!mbar_wait(&s_full[slot], phase)) {
+    for (int j = 0; j < nviews; j += 2) {
+        const int kA = K0 + j, kB = kA + 1;
+        const bool hasB = j + 1 < nviews;
+        const int slotB = slot + 1 == B2_R ? 0 : slot + 1;
+        const uint32_t phaseB = slot + 1 == B2_R ? phase ^ 1u : phase;
+        if (!mbar_wait(&s_full[slot], phase) || (hasB && !mbar_wait(&s_full[slotB], phaseB))) {
             if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
             return;  // the producer's own bounded waits end the CTA
         }
-        if (active && k >= kmin && k <= kmax) {
-            const float2 cs = s_cs[slot];
-            const float v = fmaf(-x, cs.x, fmaf(-y, cs.y, a.R));
-            const float u = fmaf(-x, cs.y, y * cs.x);
-            const float inv_v = rcp_approx(v);
-            int ci;
-            float fc;
-            column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
-            constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-            const uint32_t colx =
-                (uint32_t)(base + slot * p.slot_floats + min(max(ci - s_col[slot], 0), p.W - 2)) - (0x4B000000u << SH);
-            const float M = a.D * rsqrtf(fmaf(u, u, v * v));  // D cos(alpha*) / v*
-            const float kf = (float)(k - kbase);
-            const float ur0 = (M * z_rel(a, zb, zb_lo, kf) - a.w0row) * a.inv_dw + 1.0f;  // staged row 0 = detector row -1
-            const float dur = M * a.dz_over_dw;
-            if (k > kfull_lo && k < kfull_hi)
-                bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
-            else
-                bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+        const bool onA = active && kA >= kmin && kA <= kmax;
+        const bool onB = hasB && active && kB >= kmin && kB <= kmax;
+        if (onA || onB) {
+            const float kfA = (float)(kA - kbase);
+            ViewGeo2 g;
+            view_geo2<POLY>(a, x, y, s_cs[slot], s_cs[slotB], zb, zb_lo, kfA, g);
+            if (onA) {
+                const uint32_t colx = (uint32_t)(base + slot * p.slot_floats + min(max(g.ci0 - s_col[slot], 0), p.W - 2)) -
+                                      (0x4B000000u << SH);
+                if (kA > kfull_lo && kA < kfull_hi)
+                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, g.fc.x, g.ur0.x, g.dur.x, rmax, g.inv_v.x, kfA,
+                                                          lo, hi, acc2);
+                else
+                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, g.fc.x, g.ur0.x, g.dur.x, rmax, g.inv_v.x, kfA,
+                                                         lo, hi, acc2);
+            }
+            if (onB) {
+                const uint32_t colx =
+                    (uint32_t)(base + slotB * p.slot_floats + min(max(g.ci1 - s_col[slotB], 0), p.W - 2)) -
+                    (0x4B000000u << SH);
+                const float kfB = kfA + 1.0f;
+                if (kB > kfull_lo && kB < kfull_hi)
+                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, g.fc.y, g.ur0.y, g.dur.y, rmax, g.inv_v.y, kfB,
+                                                          lo, hi, acc2);
+                else
+                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, g.fc.y, g.ur0.y, g.dur.y, rmax, g.inv_v.y, kfB,
+                                                         lo, hi, acc2);
+            }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[slot]);
+        if (lane == 0) {
+            mbar_arrive(&s_empty[slot]);
+            if (hasB) mbar_arrive(&s_empty[slotB]);
+        }
+        slot = slotB;
+        phase = phaseB;
         if (++slot == B2_R) {
             slot = 0;
             phase ^= 1u;
