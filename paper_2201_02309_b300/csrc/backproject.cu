@@ -247,49 +247,17 @@ __device__ __forceinline__ float angle_cols(const BPArgs &a, float t)
     return atanf(t) * a.inv_da;
 }
 
-// One tap of one slice: bilinear sample at (column colx + fc, row ur) of the
-// staged window, smem[colx + (row << log2 PITCH)] (colx carries the -2^23
-// row-bias of the floor trick, in modulo-2^32 arithmetic), accumulated with
-// weight w.  CLAMP keeps the row inside the staged window (needed whenever
-// the plan cannot prove rows stay within one row of the detector).
+// Two slices' taps: bilinear samples at column colx + fc and rows ur2.x,
+// ur2.y of the staged window, smem[colx + (row << log2 PITCH)] (colx carries
+// the -2^23 row-bias of the floor trick, in modulo-2^32 arithmetic), in packed
+// FP32x2 arithmetic: every component is rounded exactly as the scalar tap rounds it
+// (a - b is formed as fma(b, -1, a)), at half the instruction count.  The
+// 16-bit forms read row-pair words (g[r-1][c] low, g[r][c] high): fp16 lerps
+// the column pair in half2 as the scalar tap does, bf16 unpacks exactly to
+// FP32 first.
 template <int PITCH, int MODE, bool CLAMP>
-__device__ __forceinline__ void bp_tap(const float *smem, uint32_t colx, float fc, __half2 fch, float ur, float rmax,
-                                       float w, float &acc)
-{
-    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-    if (CLAMP) ur = fminf(fmaxf(ur, 0.0f), rmax);
-    const float yv = __fadd_rd(ur, 8388608.0f);  // 2^23 + floor(ur), ur >= 0
-    const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
-    const float fr = ur - (yv - 8388608.0f);
-    float top, bot;
-    if (MODE == 0) {
-        const float v00 = smem[q], v01 = smem[q + 1], v10 = smem[q + PITCH], v11 = smem[q + PITCH + 1];
-        top = fmaf(fc, v01 - v00, v00);
-        bot = fmaf(fc, v11 - v10, v10);
-    } else if (MODE == 2) {
-        // each staged word holds the row pair (g[r-1][c], g[r][c]); fp16 interpolates
-        // the column pair in packed half2 arithmetic
-        const __half2 a = reinterpret_cast<const __half2 *>(smem)[q];
-        const __half2 b = reinterpret_cast<const __half2 *>(smem)[q + 1];
-        const __half2 m = __hfma2(fch, __hsub2(b, a), a);
-        top = __low2float(m);
-        bot = __high2float(m);
-    } else {
-        // bf16 keeps 8 fraction bits: interpolate in FP32 after the (exact) unpacking
-        const float2 a = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(smem)[q]);
-        const float2 b = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(smem)[q + 1]);
-        top = fmaf(fc, b.x - a.x, a.x);
-        bot = fmaf(fc, b.y - a.y, a.y);
-    }
-    acc = fmaf(w, fmaf(fr, bot - top, top), acc);
-}
-
-// Two slices' taps (rows ur2.x, ur2.y, same column) in packed FP32x2
-// arithmetic: every component is rounded exactly as the scalar tap rounds it
-// (a - b is formed as fma(b, -1, a)), at half the instruction count.
-template <int PITCH, bool CLAMP>
-__device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2 fc2, float2 ur2, float rmax,
-                                        float2 w2, float2 &acc2)
+__device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2 fc2, __half2 fch, float2 ur2,
+                                        float rmax, float2 w2, float2 &acc2)
 {
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
     if (CLAMP) {
@@ -301,58 +269,56 @@ __device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2
     const uint32_t q0 = colx + ((uint32_t)__float_as_int(yv.x) << SH);
     const uint32_t q1 = colx + ((uint32_t)__float_as_int(yv.y) << SH);
     const float2 fr = __ffma2_rn(__fadd2_rn(yv, make_float2(-8388608.0f, -8388608.0f)), m1, ur2);
-    const float2 v00 = make_float2(smem[q0], smem[q1]);
-    const float2 v01 = make_float2(smem[q0 + 1], smem[q1 + 1]);
-    const float2 v10 = make_float2(smem[q0 + PITCH], smem[q1 + PITCH]);
-    const float2 v11 = make_float2(smem[q0 + PITCH + 1], smem[q1 + PITCH + 1]);
-    const float2 top = __ffma2_rn(fc2, __ffma2_rn(v00, m1, v01), v00);
-    const float2 bot = __ffma2_rn(fc2, __ffma2_rn(v10, m1, v11), v10);
+    float2 top, bot;
+    if (MODE == 0) {
+        const float2 v00 = make_float2(smem[q0], smem[q1]);
+        const float2 v01 = make_float2(smem[q0 + 1], smem[q1 + 1]);
+        const float2 v10 = make_float2(smem[q0 + PITCH], smem[q1 + PITCH]);
+        const float2 v11 = make_float2(smem[q0 + PITCH + 1], smem[q1 + PITCH + 1]);
+        top = __ffma2_rn(fc2, __ffma2_rn(v00, m1, v01), v00);
+        bot = __ffma2_rn(fc2, __ffma2_rn(v10, m1, v11), v10);
+    } else if (MODE == 2) {
+        const __half2 *h = reinterpret_cast<const __half2 *>(smem);
+        const __half2 c0 = __hfma2(fch, __hsub2(h[q0 + 1], h[q0]), h[q0]);
+        const __half2 c1 = __hfma2(fch, __hsub2(h[q1 + 1], h[q1]), h[q1]);
+        top = make_float2(__low2float(c0), __low2float(c1));
+        bot = make_float2(__high2float(c0), __high2float(c1));
+    } else {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(smem);
+        const uint32_t a0 = w[q0], b0 = w[q0 + 1], a1 = w[q1], b1 = w[q1 + 1];
+        const float2 ta = make_float2(__uint_as_float(a0 << 16), __uint_as_float(a1 << 16));
+        const float2 tb = make_float2(__uint_as_float(b0 << 16), __uint_as_float(b1 << 16));
+        const float2 ba = make_float2(__uint_as_float(a0 & 0xFFFF0000u), __uint_as_float(a1 & 0xFFFF0000u));
+        const float2 bb = make_float2(__uint_as_float(b0 & 0xFFFF0000u), __uint_as_float(b1 & 0xFFFF0000u));
+        top = __ffma2_rn(fc2, __ffma2_rn(ta, m1, tb), ta);
+        bot = __ffma2_rn(fc2, __ffma2_rn(ba, m1, bb), ba);
+    }
     acc2 = __ffma2_rn(w2, __ffma2_rn(fr, __ffma2_rn(top, m1, bot), top), acc2);
 }
 
-// One view's contribution to a thread's B2_T slices (accumulators in pairs).
-// WEIGHTED: the view ends some slice's PI window (end weights; slices outside
-// their window are skipped).  FP32 data runs slice pairs in FP32x2; a pair
-// with one slice outside its window still loads that slice's taps (weight
-// zero), so weighted pairs always clamp.  The scalar 16-bit forms skip such
-// slices, so every tap they take lies in a PI window and CLAMP follows the
-// plan's row proof; otherwise every slice takes the view with weight 1.
+// One view's contribution to a thread's B2_T slices, in slice pairs.
+// WEIGHTED: the view ends some slice's PI window (end weights, zero outside
+// it; a pair with neither slice in its window is skipped, one with a single
+// such slice still loads its taps, so weighted pairs always clamp);
+// otherwise every slice takes the view with weight 1.
 template <int PITCH, int MODE, bool WEIGHTED, bool CLAMP>
 __device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
                                         float inv_v, float kf, const float *lo, const float *hi, float2 *acc2)
 {
-    if (MODE == 0 && !WEIGHTED) {
-        const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
-        const float2 w2 = make_float2(inv_v, inv_v);
+    const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
+    const __half2 fch = __float2half2_rn(fc);
 #pragma unroll
-        for (int pr = 0; pr < B2_T / 2; ++pr)
-            bp_tap2<PITCH, CLAMP>(smem, colx, fc2, __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02), rmax, w2,
-                                  acc2[pr]);
-        return;
-    }
-    if (MODE == 0 && WEIGHTED) {
-        const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
-#pragma unroll
-        for (int pr = 0; pr < B2_T / 2; ++pr) {
+    for (int pr = 0; pr < B2_T / 2; ++pr) {
+        const float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
+        if (WEIGHTED) {
             const float om0 = __saturatef(kf - lo[2 * pr]) * __saturatef(hi[2 * pr] - kf);
             const float om1 = __saturatef(kf - lo[2 * pr + 1]) * __saturatef(hi[2 * pr + 1] - kf);
             if (om0 == 0.0f && om1 == 0.0f) continue;
-            bp_tap2<PITCH, true>(smem, colx, fc2, __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02), rmax,
-                                 make_float2(om0 * inv_v, om1 * inv_v), acc2[pr]);
+            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, make_float2(om0 * inv_v, om1 * inv_v),
+                                       acc2[pr]);
+        } else {
+            bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), acc2[pr]);
         }
-        return;
-    }
-    const __half2 fch = __float2half2_rn(fc);
-#pragma unroll
-    for (int t = 0; t < B2_T; ++t) {
-        float w = inv_v;
-        if (WEIGHTED) {
-            const float om = __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
-            if (om == 0.0f) continue;
-            w = om * inv_v;
-        }
-        bp_tap<PITCH, MODE, CLAMP>(smem, colx, fc, fch, fmaf((float)t, dur, ur0), rmax, w,
-                                   (t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x);
     }
 }
 
