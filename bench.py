@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
     ap.add_argument("--turns", type=int, default=None, help="fewer helix turns (profiling captures only)")
+    ap.add_argument("--requests", type=int, default=256, help="config 5: requests in the stream")
+    ap.add_argument("--slots", type=int, default=4, help="config 5: concurrent requests (CUDA streams)")
+    ap.add_argument("--arena-gb", type=float, default=24.0, help="config 5: device arena for running requests")
+    ap.add_argument("--plan-cache-gb", type=float, default=16.0, help="config 5: device plan cache")
     return ap.parse_args()
 
 
@@ -355,10 +359,163 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------- serving form
+SERVING_VOLUMES = [(128, 128, 32), (256, 256, 64), (512, 512, 128)]
+SERVING_VPT = [256, 580, 1160]
+SERVING_DETECTORS = [(736, 1), (368, 2), (184, 4)]  # columns kept, every col_keep-th of the 736
+SERVING_PITCH = [1.0, 1.25, 1.5]
+
+
+def serving_protocols(kats, n_protocols=12, seed=7):
+    """Scan protocols of the serving mix, drawn (seeded) from the product of the
+    volume sizes, views per turn, detector column sets and pitch factors; the
+    clinical scanner (R 595, D 1085.6, 64 rows).  Turns: the volume's pitches
+    plus two, so every PI window lies inside the scan."""
+    import math
+
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_protocols):
+        (nx, ny, nz) = SERVING_VOLUMES[rng.integers(3)]
+        vpt = SERVING_VPT[rng.integers(3)]
+        cols, keep = SERVING_DETECTORS[rng.integers(3)]
+        pf = SERVING_PITCH[rng.integers(3)]
+        cfg = dict(R=595.0, D=1085.6, views_per_turn=vpt, turns=1, n_rows=64, n_cols=cols, n_cols_full=736,
+                   col_keep=keep, det_half_width=256.0, nx=nx, ny=ny, nz=nz, voxel=1.0, pitch_factor=pf)
+        g = kats.make_geometry(cfg)
+        cfg["turns"] = int(math.ceil(nz * g["dz"] / g["P"])) + 2
+        out.append(kats.make_geometry(cfg))
+    return out
+
+
+def run_serving(args):
+    """Config 5: a seeded Poisson stream of requests over mixed protocols,
+    served with continuous batching; p50/p99 latency and vol/s, next to the
+    plain FP32 path (one request at a time through katsevich_recon_host)."""
+    import collections
+
+    import numpy as np
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    from paper_2201_02309_b300 import build, native
+    from paper_2201_02309_b300.serving import Server
+    build.build()
+    n_req, slots, seed = args.requests, args.slots, 7
+    prec = {"fp32": kats.KATS_PREC_FP32, "bf16": kats.KATS_PREC_BF16, "fp16": kats.KATS_PREC_FP16}[args.precision]
+    protos = serving_protocols(kats)
+    rng = np.random.default_rng(seed)
+    which = rng.integers(len(protos), size=n_req)
+    plans = [kats.Plan(g) for g in protos]
+    updates = [p.info["update_count"] for p in plans]
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    sinos = []
+    for g in protos:
+        s = torch.empty((g["n_views"], g["n_rows"], g["n_cols"]), dtype=torch.float32, pin_memory=True)
+        s.copy_(torch.rand(s.shape, generator=gen, device="cuda"))
+        sinos.append(s)
+    max_vol = max(g["nx"] * g["ny"] * g["nz"] for g in protos)
+    depth = 3 * slots
+    pool = [torch.empty(max_vol, dtype=torch.float32, pin_memory=True) for _ in range(depth)]
+
+    def vol_view(buf, g):
+        return buf[: g["nz"] * g["ny"] * g["nx"]].view(g["nz"], g["ny"], g["nx"])
+
+    # plain FP32 path: one request at a time, synchronous, plans built beforehand
+    ws = torch.empty(max(native.load().katsevich_host_workspace_bytes(p.handle, 1, kats.KATS_PREC_FP32)
+                         for p in plans), dtype=torch.uint8, device="cuda")
+    for k in range(len(protos)):  # warm-up
+        plans[k].recon_host(sinos[k], vol_view(pool[0], protos[k]), workspace=ws)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in which:
+        plans[int(k)].recon_host(sinos[k], vol_view(pool[0], protos[k]), workspace=ws)
+    plain_s = time.perf_counter() - t
+    mu = n_req / plain_s  # single-stream capacity, requests/s
+    del ws
+    torch.cuda.empty_cache()
+
+    arena = int(args.arena_gb * (1 << 30))
+
+    def serve(arrivals, closed_loop):
+        """Submit request i at arrivals[i] (seconds; closed loop: as soon as fewer
+        than `depth` are outstanding).  Returns latencies (ms), makespan (s), stats."""
+        lat, free, out = [None] * n_req, list(range(depth)), collections.deque()
+        first_submit, last_done = None, 0.0
+        with Server(arena_bytes=arena, plan_cache_bytes=int(args.plan_cache_gb * (1 << 30)), slots=slots,
+                    max_bypass=2 * slots) as srv:
+            for k in range(len(protos)):  # plans cached on the device before the stream starts
+                srv.wait(srv.submit(protos[k], sinos[k], vol_view(pool[0], protos[k]), precision=prec))
+            t0 = time.perf_counter()
+            i = 0
+            while i < n_req or out:
+                now = time.perf_counter() - t0
+                if i < n_req and free and (closed_loop or now >= arrivals[i]):
+                    k, b = int(which[i]), free.pop()
+                    tk = srv.submit(protos[k], sinos[k], vol_view(pool[b], protos[k]), precision=prec)
+                    late = 0.0 if closed_loop else (time.perf_counter() - t0) - arrivals[i]
+                    out.append((i, tk, b, late))
+                    i += 1
+                    continue
+                if out:
+                    j, tk, b, late = out[0]
+                    rc, st, msg = native.katsevich_server_wait(srv.handle, tk.id, 0)
+                    if rc == native.KATS_ETIMEOUT:
+                        time.sleep(0.0002)
+                        continue
+                    if rc != native.KATS_OK:
+                        raise kats.KatsevichError(rc, msg)
+                    out.popleft()
+                    free.append(b)
+                    lat[j] = (st["t_done_ms"] - st["t_submit_ms"]) + 1e3 * late
+                    last_done = max(last_done, st["t_done_ms"])
+                    if j == 0:
+                        first_submit = st["t_submit_ms"] - 1e3 * late
+                elif i < n_req:
+                    time.sleep(max(0.0, min(0.001, arrivals[i] - now)))
+            stats = srv.stats()
+        return lat, (last_done - first_submit) / 1e3, stats
+
+    clocks = Clocks(0)
+    clocks.start()
+    lat_sat, span_sat, st_sat = serve(None, True)
+    runs = {}
+    for rho in (0.5, 0.8, 1.0):
+        gaps = np.random.default_rng(seed).exponential(1.0 / (rho * mu), size=n_req)
+        lat, span, st = serve(np.cumsum(gaps) - gaps[0], False)
+        runs[str(rho)] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "vol_per_s": n_req / span, "max_running": st["max_running"]}
+    clk = clocks.stop()
+    upd = float(sum(updates[int(k)] for k in which))
+    line = {
+        "metric": METRIC, "value": n_req / span_sat, "unit": "vol/s", "n_gpus": 1, "steps": n_req, "warmup": len(protos),
+        "ms_per_step": 1e3 * span_sat / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision], "data": "synthetic",
+        "config": {"workload": "serving_mix_poisson_256", "protocols": len(protos), "requests": n_req,
+                   "slots": slots, "arena_gb": args.arena_gb, "precision": args.precision,
+                   "volumes": SERVING_VOLUMES, "views_per_turn": SERVING_VPT, "detector_cols": SERVING_DETECTORS,
+                   "pitch_factors": SERVING_PITCH, "seed": seed},
+        "serving": {
+            "saturated": {"vol_per_s": n_req / span_sat, "gups": upd / span_sat / 1e9,
+                          "p50_ms": float(np.percentile(lat_sat, 50)), "p99_ms": float(np.percentile(lat_sat, 99)),
+                          "max_running": st_sat["max_running"], "arena_peak_gb": st_sat["arena_peak_bytes"] / 2**30},
+            "poisson": runs,
+            "plain_fp32": {"vol_per_s": mu, "gups": upd / plain_s / 1e9,
+                           "note": "one request at a time through katsevich_recon_host (H2D, recon, D2H)"},
+            "served_over_plain": (n_req / span_sat) / mu,
+        },
+        "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 5:
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -64,8 +64,9 @@ extern "C" {
 /* Storage precision of the intermediate data (precision form of the operator):
  * FP32 everywhere, or the rebinned derivative data and the filtered data g^F
  * stored in BF16 / FP16 (scaled by d_alpha), the Hilbert contraction on 16-bit
- * tensor cores with the Toeplitz operand split hi + lo, interpolation of the
- * column pair in packed 16-bit arithmetic, and FP32 accumulation.  The reduced
+ * tensor cores with the Toeplitz operand split hi + lo, and FP32 accumulation
+ * (FP16 interpolates the detector column pair in packed half arithmetic, BF16
+ * unpacks exactly to FP32 first).  The reduced
  * forms are available for katsevich_recon and katsevich_recon_host; every other
  * entry point takes KATS_PREC_FP32. */
 #define KATS_PREC_FP32 0
@@ -257,6 +258,93 @@ KATS_API int katsevich_recon_noalloc(const kats_plan *plan, const float *sino, f
  * clears it.
  */
 KATS_API int katsevich_device_status(const kats_plan *plan, int *status);
+
+/*
+ * Serving loop (the operator's deployment form; the paper has no counterpart).
+ *
+ * A server owns CUDA streams ("slots"), one device arena and a device plan
+ * cache.  katsevich_server_submit queues a request (any geometry, volume size
+ * and precision; host sinogram in, host volume out) and returns at once.  A
+ * worker thread admits queued requests in arrival order as soon as a slot is
+ * free and the request's device block (view window + volume + workspace,
+ * katsevich_host_workspace_bytes of its plan) fits in the arena; requests that
+ * arrive while others run are admitted as slots and memory free up, and
+ * their copies and kernels overlap on the device (continuous batching).  A
+ * request whose block does not fit waits; later requests may be admitted
+ * ahead of the first one in line at most max_bypass times, then admission
+ * waits for it.  A request larger than the whole arena completes with
+ * KATS_ENOMEM ("refused").  Plans are built on first use (on the worker
+ * thread, on a private stream) and cached by geometry; when the cache's plans
+ * exceed plan_cache_bytes, idle plans are destroyed least recently used first
+ * (destroying one may wait for the device).
+ *
+ * Ownership: host_sino (the full sinogram [n_views][n_rows][n_cols]) and
+ * host_vol ([nz][ny][nx]) are the caller's and must stay valid until
+ * katsevich_server_wait has returned for the ticket; page-locked buffers let
+ * the copies overlap other requests' kernels (pageable ones still work, with
+ * the copies serialised).  Results are bit-identical to katsevich_recon_host
+ * on the same plan and precision: each request runs the same kernels on its
+ * own block.
+ *
+ * Errors: create/submit/wait return KATS_* codes.  wait returns the request's
+ * own status (a failed plan build: its code; a device wait that gave up inside
+ * the request's kernels: KATS_ETIMEOUT) and releases the ticket; if the request
+ * has not finished after timeout_ms (negative = do not wait) it returns
+ * KATS_ETIMEOUT and the ticket stays valid.  Destroying the server finishes the
+ * running requests, fails the queued ones and invalidates every ticket.
+ */
+typedef struct kats_server kats_server;
+typedef struct kats_server_config {
+    int64_t arena_bytes;      /* device bytes for the running requests' blocks (one allocation)  */
+    int64_t plan_cache_bytes; /* device bytes of cached plans before idle ones are evicted        */
+    int32_t slots;            /* concurrent requests, one CUDA stream each (1 .. 64)              */
+    int32_t max_bypass;       /* later requests admitted ahead of a waiting first-in-line one     */
+} kats_server_config;
+typedef struct kats_request_stats {
+    int32_t status;       /* the request's KATS_* status                                   */
+    int32_t slot;         /* slot it ran on (-1 if never admitted)                          */
+    int32_t plan_hit;     /* 1 if its plan was already cached when it was first considered  */
+    int32_t bypassed;     /* requests admitted ahead of it while it was first in line       */
+    double t_submit_ms;   /* host clock (ms since the server started): submitted            */
+    double t_admit_ms;    /*   admitted (slot and block assigned, work issued)              */
+    double t_done_ms;     /*   completion seen by the worker                                */
+    double gpu_ms;        /* device time of its stream work (copies + kernels), CUDA events */
+    int64_t device_bytes; /* arena bytes it held                                            */
+} kats_request_stats;
+typedef struct kats_server_stats {
+    int64_t submitted, completed, failed, refused;
+    int64_t plan_hits, plan_misses, plan_evictions, plans_cached;
+    int64_t arena_bytes, arena_in_use_bytes, arena_peak_bytes, plan_cache_used_bytes;
+    int32_t slots, max_running, pending, running;
+} kats_server_stats;
+KATS_API int katsevich_server_create(const kats_server_config *cfg, kats_server **out);
+KATS_API int katsevich_server_submit(kats_server *srv, const kats_geometry *g, const float *host_sino,
+                                     float *host_vol, int precision, uint64_t *ticket);
+KATS_API int katsevich_server_wait(kats_server *srv, uint64_t ticket, int64_t timeout_ms, kats_request_stats *stats);
+KATS_API int katsevich_server_stats(kats_server *srv, kats_server_stats *out);
+KATS_API void katsevich_server_destroy(kats_server *srv);
+
+/*
+ * The server's admission arena as a host-only object (no device memory is
+ * touched): first-fit offsets in [0, bytes), blocks rounded up to 256 bytes,
+ * freed neighbours merged.  alloc returns an offset or -1 when no free block
+ * fits; free returns KATS_EINVAL for an offset that is not an allocated block.
+ */
+typedef struct kats_arena kats_arena;
+KATS_API int katsevich_arena_create(int64_t bytes, kats_arena **out);
+KATS_API int64_t katsevich_arena_alloc(kats_arena *a, int64_t bytes);
+KATS_API int katsevich_arena_free(kats_arena *a, int64_t offset);
+KATS_API int64_t katsevich_arena_largest_free(const kats_arena *a);
+KATS_API int64_t katsevich_arena_in_use(const kats_arena *a);
+KATS_API void katsevich_arena_destroy(kats_arena *a);
+
+/*
+ * Host-side fault injection for tests: the next n device allocations the
+ * library makes (plan tables and scratch, a server's arena) fail as if the
+ * device were out of memory, without calling CUDA; the call then returns
+ * KATS_ENOMEM.  n <= 0 switches injection off.
+ */
+KATS_API void katsevich_debug_fail_allocs(int n);
 
 /* Release a plan's device memory.  NULL is allowed. */
 KATS_API void katsevich_plan_destroy(kats_plan *plan);

@@ -6,6 +6,10 @@ The operator is linear, f = A g, so dL/dg = A^T dL/df needs no activations:
 the backward pass keeps only the plan.  Pitch-by-pitch training (one
 sinogram window per step, as the paper trains) therefore checkpoints nothing
 beyond the window itself.
+
+With a reduced-precision forward (BF16 / FP16 storage of the intermediate
+data) the backward is still the FP32 transpose: it is the exact adjoint of the
+operator the reduced form approximates, within the reduced form's tolerance.
 """
 from __future__ import annotations
 
@@ -25,7 +29,7 @@ class KatsevichFunction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_vol: torch.Tensor):
-        grad = ctx.plan.adjoint(grad_vol.contiguous(), precision=ctx.precision) if ctx.needs_input_grad[0] else None
+        grad = ctx.plan.adjoint(grad_vol.contiguous()) if ctx.needs_input_grad[0] else None
         return grad, None, None
 
 

@@ -74,6 +74,32 @@ size_t adjoint_ws(const Plan &p) { return align256(gf_bytes(p)) + filter_adjoint
 
 }  // namespace
 
+namespace kats {
+
+size_t host_item_bytes(const Plan &p, int precision)
+{
+    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
+    return align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws_for(p, precision);
+}
+
+// One item from host buffers, stream-ordered and asynchronous: copy the view
+// window the volume needs, steps 1-7, copy the volume back.  ws holds
+// host_item_bytes(p, precision) bytes.
+int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
+{
+    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
+    float *d_win = (float *)ws;
+    float *d_vol = (float *)((char *)ws + align256(win));
+    char *rws = (char *)d_vol + align256(sizeof(float) * vol_item(p));
+    KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + p.first_view * view_elems(p), win, cudaMemcpyHostToDevice, st));
+    int rc = recon_item(p, precision, d_win, d_vol, rws, recon_ws_for(p, precision), st);
+    if (rc) return rc;
+    KATS_CUDA(cudaMemcpyAsync(host_vol, d_vol, sizeof(float) * vol_item(p), cudaMemcpyDeviceToHost, st));
+    return KATS_OK;
+}
+
+}  // namespace kats
+
 extern "C" {
 
 int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision)
@@ -200,9 +226,7 @@ int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int pre
     if (!plan || batch < 1 || (precision != KATS_PREC_FP32 && precision != KATS_PREC_BF16 &&
                                precision != KATS_PREC_FP16))
         return -1;
-    const Plan &p = *reinterpret_cast<const Plan *>(plan);
-    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
-    return (int64_t)(align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws_for(p, precision));
+    return (int64_t)host_item_bytes(*reinterpret_cast<const Plan *>(plan), precision);
 }
 
 int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch, int precision,
@@ -217,18 +241,9 @@ int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *h
         return KATS_ESPACE;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
-    float *d_win = (float *)workspace;
-    float *d_vol = (float *)((char *)workspace + align256(win));
-    char *rws = (char *)d_vol + align256(sizeof(float) * vol_item(p));
-    const size_t rws_bytes = recon_ws_for(p, precision);
     for (int b = 0; b < batch; ++b) {
-        KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + b * sino_item(p) + p.first_view * view_elems(p), win,
-                                  cudaMemcpyHostToDevice, st));
-        rc = recon_item(p, precision, d_win, d_vol, rws, rws_bytes, st);
+        rc = recon_one_host(p, precision, host_sino + b * sino_item(p), host_vol + b * vol_item(p), workspace, st);
         if (rc) return rc;
-        KATS_CUDA(cudaMemcpyAsync(host_vol + b * vol_item(p), d_vol, sizeof(float) * vol_item(p),
-                                  cudaMemcpyDeviceToHost, st));
     }
     KATS_CUDA(cudaStreamSynchronize(st));
     return KATS_OK;

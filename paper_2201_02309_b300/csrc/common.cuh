@@ -92,4 +92,13 @@ size_t filter_workspace_bytes(const Plan &p);
 int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done);
 size_t filter_adjoint_workspace_bytes(const Plan &p);
 
+// one item from host buffers (api.cu): device bytes it needs, and the
+// stream-ordered H2D window copy + steps 1-7 + D2H volume copy
+size_t host_item_bytes(const Plan &p, int precision);
+int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st);
+
+// device allocations that honour the test hook katsevich_debug_fail_allocs (plan.cu)
+cudaError_t dev_malloc(void **ptr, size_t bytes);
+cudaError_t dev_malloc_async(void **ptr, size_t bytes, cudaStream_t st);
+
 }  // namespace kats

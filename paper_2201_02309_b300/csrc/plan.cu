@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace kats {
@@ -24,6 +26,37 @@ int cuda_fail(cudaError_t e, const char *what)
 {
     set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
     return (e == cudaErrorMemoryAllocation) ? KATS_ENOMEM : KATS_ECUDA;
+}
+
+// Host-side fault injection for tests: the next g_fail_allocs device
+// allocations made through dev_malloc / dev_malloc_async report
+// cudaErrorMemoryAllocation without calling CUDA.
+static std::atomic<int> g_fail_allocs{0};
+
+static bool inject_alloc_failure()
+{
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
+cudaError_t dev_malloc(void **ptr, size_t bytes)
+{
+    if (inject_alloc_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t dev_malloc_async(void **ptr, size_t bytes, cudaStream_t st)
+{
+    if (inject_alloc_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(ptr, bytes, st);
 }
 
 // ------------------------------------------------- host 16-bit conversions
@@ -486,7 +519,7 @@ static void free_plan(Plan *p)
 template <class T>
 static int dalloc(Plan *p, T **ptr, size_t count)
 {
-    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * (count ? count : 1));
+    cudaError_t e = dev_malloc((void **)ptr, sizeof(T) * (count ? count : 1));
     if (e != cudaSuccess) {
         *ptr = nullptr;
         return cuda_fail(e, "cudaMalloc(plan table)");
@@ -513,7 +546,23 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->bt16_hi[0], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[0], p->tc_n * p->tc_k16)) ||
         (rc = dalloc(p, &p->bt16_hi[1], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[1], p->tc_n * p->tc_k16)))
         return rc;
-    KATS_CUDA(cudaMemset(p->dev_status, 0, sizeof(int)));
+    // Everything below runs on a private non-blocking stream (host tables are
+    // copied with stream-ordered copies, scratch is stream-ordered), so
+    // building a plan waits only for its own work: requests running on other
+    // streams, e.g. in the serving loop, keep going.
+    struct StreamGuard {
+        cudaStream_t s = nullptr;
+        ~StreamGuard()
+        {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } guard;
+    KATS_CUDA(cudaStreamCreateWithFlags(&guard.s, cudaStreamNonBlocking));
+    cudaStream_t st = guard.s;
+    KATS_CUDA(cudaMemsetAsync(p->dev_status, 0, sizeof(int), st));
 
     // small 1-D tables in FP64 on the host, stored FP32
     {
@@ -532,11 +581,11 @@ static int build(Plan *p)
             trig[k] = make_float2((float)c, (float)s);
             trig_lo[k] = make_float2((float)(c - (double)(float)c), (float)(s - (double)(float)s));
         }
-        KATS_CUDA(cudaMemcpy(p->hk, hk.data(), hk.size() * sizeof(float), cudaMemcpyHostToDevice));
-        KATS_CUDA(cudaMemcpy(p->lw, lw.data(), lw.size() * sizeof(float), cudaMemcpyHostToDevice));
-        KATS_CUDA(cudaMemcpy(p->cosa, cosa.data(), cosa.size() * sizeof(float), cudaMemcpyHostToDevice));
-        KATS_CUDA(cudaMemcpy(p->trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice));
-        KATS_CUDA(cudaMemcpy(p->trig_lo, trig_lo.data(), trig_lo.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        KATS_CUDA(cudaMemcpyAsync(p->hk, hk.data(), hk.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->lw, lw.data(), lw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->cosa, cosa.data(), cosa.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->trig_lo, trig_lo.data(), trig_lo.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
         std::vector<float> bhi((size_t)(p->tc_n * p->tc_k), 0.0f), blo((size_t)(p->tc_n * p->tc_k), 0.0f);
         for (int64_t c = 0; c < nc; ++c)
             for (int64_t cp = 0; cp < p->nc1; ++cp) {
@@ -549,8 +598,8 @@ static int build(Plan *p)
                 bhi[(size_t)(c * p->tc_k + cp)] = hi;
                 blo[(size_t)(c * p->tc_k + cp)] = v - hi;
             }
-        KATS_CUDA(cudaMemcpy(p->bt_hi, bhi.data(), bhi.size() * sizeof(float), cudaMemcpyHostToDevice));
-        KATS_CUDA(cudaMemcpy(p->bt_lo, blo.data(), blo.size() * sizeof(float), cudaMemcpyHostToDevice));
+        KATS_CUDA(cudaMemcpyAsync(p->bt_hi, bhi.data(), bhi.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->bt_lo, blo.data(), blo.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         // 16-bit pairs: hi = value rounded to the type, lo = remainder rounded to the type
         const size_t n16 = (size_t)(p->tc_n * p->tc_k16);
         std::vector<uint16_t> h16(n16, 0), l16(n16, 0);
@@ -571,60 +620,53 @@ static int build(Plan *p)
                         l16[o] = host_to_fp16(v - host_from_fp16(hb));
                     }
                 }
-            KATS_CUDA(cudaMemcpy(p->bt16_hi[kind], h16.data(), n16 * 2, cudaMemcpyHostToDevice));
-            KATS_CUDA(cudaMemcpy(p->bt16_lo[kind], l16.data(), n16 * 2, cudaMemcpyHostToDevice));
+            KATS_CUDA(cudaMemcpyAsync(p->bt16_hi[kind], h16.data(), n16 * 2, cudaMemcpyHostToDevice, st));
+            KATS_CUDA(cudaMemcpyAsync(p->bt16_lo[kind], l16.data(), n16 * 2, cudaMemcpyHostToDevice, st));
         }
     }
-
-    k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256>>>(G, p->kap_idx, p->kap_frac);
-    KATS_CUDA(cudaGetLastError());
-    k_plan_psi<<<(unsigned)ceil_div(nr * nc, 128), 128>>>(G, p->psi_idx, p->psi_frac);
-    KATS_CUDA(cudaGetLastError());
 
     double *lam_i = nullptr, *lam_o = nullptr, *lmin_part = nullptr, *lmax_part = nullptr;
     unsigned long long *sums = nullptr;
     float *ext_part = nullptr;
     const int ext_blocks = 148 * 8;
     auto cleanup = [&]() {
-        if (lam_i) cudaFree(lam_i);
-        if (lam_o) cudaFree(lam_o);
-        if (lmin_part) cudaFree(lmin_part);
-        if (lmax_part) cudaFree(lmax_part);
-        if (sums) cudaFree(sums);
-        if (ext_part) cudaFree(ext_part);
+        for (void *q : {(void *)lam_i, (void *)lam_o, (void *)lmin_part, (void *)lmax_part, (void *)sums,
+                        (void *)ext_part})
+            if (q) cudaFreeAsync(q, st);
     };
-    cudaError_t e;
-    if ((e = cudaMalloc(&lam_i, sizeof(double) * N * nxy)) != cudaSuccess ||
-        (e = cudaMalloc(&lam_o, sizeof(double) * N * nxy)) != cudaSuccess ||
-        (e = cudaMalloc(&lmin_part, sizeof(double) * N)) != cudaSuccess ||
-        (e = cudaMalloc(&lmax_part, sizeof(double) * N)) != cudaSuccess ||
-        (e = cudaMalloc(&sums, sizeof(unsigned long long) * N)) != cudaSuccess ||
-        (e = cudaMalloc(&ext_part, sizeof(float) * 4 * ext_blocks)) != cudaSuccess) {
-        cleanup();
-        return cuda_fail(e, "cudaMalloc(plan scratch)");
-    }
-    k_plan_pi<<<(unsigned)ceil_div(N * nxy, 128), 128>>>(G, p->pi_k0, p->pi_k1, p->pi_w0, p->pi_w1, lam_i, lam_o);
-    k_slice_reduce<<<(unsigned)N, 256>>>(nxy, p->pi_k0, p->pi_k1, lam_i, lam_o, p->slice_kmin, p->slice_kmax,
-                                        sums, lmin_part, lmax_part);
-    k_extents<<<ext_blocks, 256>>>(G, p->pi_k0, p->pi_k1, p->trig, ext_part);
-    e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaGetLastError();
+    k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256, 0, st>>>(G, p->kap_idx, p->kap_frac);
+    k_plan_psi<<<(unsigned)ceil_div(nr * nc, 128), 128, 0, st>>>(G, p->psi_idx, p->psi_frac);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&lam_i, sizeof(double) * N * nxy, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&lam_o, sizeof(double) * N * nxy, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&lmin_part, sizeof(double) * N, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&lmax_part, sizeof(double) * N, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&sums, sizeof(unsigned long long) * N, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&ext_part, sizeof(float) * 4 * ext_blocks, st);
     if (e != cudaSuccess) {
         cleanup();
-        return cuda_fail(e, "plan kernels");
+        return cuda_fail(e, "plan scratch allocation");
     }
+    k_plan_pi<<<(unsigned)ceil_div(N * nxy, 128), 128, 0, st>>>(G, p->pi_k0, p->pi_k1, p->pi_w0, p->pi_w1, lam_i,
+                                                                 lam_o);
+    k_slice_reduce<<<(unsigned)N, 256, 0, st>>>(nxy, p->pi_k0, p->pi_k1, lam_i, lam_o, p->slice_kmin,
+                                               p->slice_kmax, sums, lmin_part, lmax_part);
+    k_extents<<<ext_blocks, 256, 0, st>>>(G, p->pi_k0, p->pi_k1, p->trig, ext_part);
+    e = cudaGetLastError();
     std::vector<int32_t> kmin(N), kmax(N);
     std::vector<unsigned long long> hs(N);
     std::vector<double> lmin(N), lmax(N);
     std::vector<float> ext(4 * ext_blocks);
-    e = cudaMemcpy(kmin.data(), p->slice_kmin, sizeof(int32_t) * N, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(kmax.data(), p->slice_kmax, sizeof(int32_t) * N, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), sums, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(lmin.data(), lmin_part, sizeof(double) * N, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(lmax.data(), lmax_part, sizeof(double) * N, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(ext.data(), ext_part, sizeof(float) * 4 * ext_blocks, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kmin.data(), p->slice_kmin, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kmax.data(), p->slice_kmax, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), sums, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lmin.data(), lmin_part, sizeof(double) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lmax.data(), lmax_part, sizeof(double) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ext.data(), ext_part, sizeof(float) * 4 * ext_blocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(plan reductions)");
+    if (e != cudaSuccess) return cuda_fail(e, "plan kernels and reductions");
 
     // views the whole volume needs; slice s uses table slice s mod N shifted by (s div N) turns
     int64_t vmin = INT64_MAX, vmax = INT64_MIN, count = 0;
@@ -666,6 +708,8 @@ using namespace kats;
 extern "C" {
 
 const char *katsevich_last_error(void) { return g_err; }
+
+void katsevich_debug_fail_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
 
 int katsevich_fit_pitch(const kats_geometry *g, double factor, double *pitch_out)
 {

@@ -21,7 +21,11 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
            "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error",
            "katsevich_recon_noalloc", "katsevich_device_status", "katsevich_backproject_adjoint",
-           "katsevich_filter_adjoint"]
+           "katsevich_filter_adjoint", "katsevich_server_create", "katsevich_server_submit",
+           "katsevich_server_wait", "katsevich_server_stats", "katsevich_server_destroy",
+           "katsevich_arena_create", "katsevich_arena_alloc", "katsevich_arena_free",
+           "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
+           "katsevich_debug_fail_allocs"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -46,6 +50,24 @@ class kats_plan_info(ctypes.Structure):
                 ("first_view", ctypes.c_int64), ("n_filtered_views", ctypes.c_int64),
                 ("update_count", ctypes.c_int64), ("gf_cols", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_int64)]
+
+
+class kats_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_int64), ("plan_cache_bytes", ctypes.c_int64),
+                ("slots", ctypes.c_int32), ("max_bypass", ctypes.c_int32)]
+
+
+class kats_request_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("plan_hit", ctypes.c_int32),
+                ("bypassed", ctypes.c_int32), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("gpu_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+class kats_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "refused", "plan_hits",
+                                              "plan_misses", "plan_evictions", "plans_cached", "arena_bytes",
+                                              "arena_in_use_bytes", "arena_peak_bytes", "plan_cache_used_bytes")] + \
+        [(n, ctypes.c_int32) for n in ("slots", "max_running", "pending", "running")]
 
 
 class KatsevichError(RuntimeError):
@@ -87,6 +109,20 @@ def load() -> ctypes.CDLL:
         "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
         "katsevich_last_error": (ctypes.c_char_p, []),
+        "katsevich_server_create": (ctypes.c_int, [ctypes.POINTER(kats_server_config), ctypes.POINTER(P)]),
+        "katsevich_server_submit": (ctypes.c_int, [P, ctypes.POINTER(kats_geometry), P, P, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_uint64)]),
+        "katsevich_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_int64,
+                                                 ctypes.POINTER(kats_request_stats)]),
+        "katsevich_server_stats": (ctypes.c_int, [P, ctypes.POINTER(kats_server_stats)]),
+        "katsevich_server_destroy": (None, [P]),
+        "katsevich_arena_create": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(P)]),
+        "katsevich_arena_alloc": (ctypes.c_int64, [P, ctypes.c_int64]),
+        "katsevich_arena_free": (ctypes.c_int, [P, ctypes.c_int64]),
+        "katsevich_arena_largest_free": (ctypes.c_int64, [P]),
+        "katsevich_arena_in_use": (ctypes.c_int64, [P]),
+        "katsevich_arena_destroy": (None, [P]),
+        "katsevich_debug_fail_allocs": (None, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -196,3 +232,68 @@ def katsevich_plan_destroy(plan) -> None:
 
 def katsevich_last_error() -> str:
     return load().katsevich_last_error().decode(errors="replace")
+
+
+# --- serving loop ------------------------------------------------------------
+def katsevich_server_create(arena_bytes: int, plan_cache_bytes: int, slots: int, max_bypass: int = 8) -> int:
+    cfg = kats_server_config(arena_bytes, plan_cache_bytes, slots, max_bypass)
+    h = ctypes.c_void_p()
+    check(load().katsevich_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def katsevich_server_submit(server: int, geom: dict, host_sino_ptr: int, host_vol_ptr: int,
+                            precision: int = KATS_PREC_FP32) -> int:
+    g = geometry_struct(geom)
+    t = ctypes.c_uint64()
+    check(load().katsevich_server_submit(server, ctypes.byref(g), host_sino_ptr, host_vol_ptr, precision,
+                                         ctypes.byref(t)))
+    return t.value
+
+
+def katsevich_server_wait(server: int, ticket: int, timeout_ms: int):
+    """(status, stats dict, message): the request's own status is returned, not raised."""
+    st = kats_request_stats()
+    rc = load().katsevich_server_wait(server, ticket, timeout_ms, ctypes.byref(st))
+    msg = load().katsevich_last_error().decode(errors="replace") if rc else ""
+    return rc, {k: getattr(st, k) for k, _ in kats_request_stats._fields_}, msg
+
+
+def katsevich_server_stats(server: int) -> dict:
+    st = kats_server_stats()
+    check(load().katsevich_server_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in kats_server_stats._fields_}
+
+
+def katsevich_server_destroy(server: int) -> None:
+    load().katsevich_server_destroy(server)
+
+
+def katsevich_arena_create(nbytes: int) -> int:
+    h = ctypes.c_void_p()
+    check(load().katsevich_arena_create(nbytes, ctypes.byref(h)))
+    return h.value
+
+
+def katsevich_arena_alloc(arena: int, nbytes: int) -> int:
+    return load().katsevich_arena_alloc(arena, nbytes)
+
+
+def katsevich_arena_free(arena: int, offset: int) -> None:
+    check(load().katsevich_arena_free(arena, offset))
+
+
+def katsevich_arena_largest_free(arena: int) -> int:
+    return load().katsevich_arena_largest_free(arena)
+
+
+def katsevich_arena_in_use(arena: int) -> int:
+    return load().katsevich_arena_in_use(arena)
+
+
+def katsevich_arena_destroy(arena: int) -> None:
+    load().katsevich_arena_destroy(arena)
+
+
+def katsevich_debug_fail_allocs(n: int) -> None:
+    load().katsevich_debug_fail_allocs(n)
