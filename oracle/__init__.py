@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  It shares no code with
 the CUDA library (``paper_2201_02309_b300``) and never imports it.
 
-The arithmetic lives in ``katsevich_oracle.c`` (plain C, FP64, OpenMP); this
-module only compiles it, marshals numpy arrays, and derives a workload's
+The arithmetic lives in ``katsevich_oracle.c`` (the reconstruction operator)
+and ``simulate_oracle.c`` (data simulation: helical projection, sparse
+detector upsampling, Gaussian+Poisson noise), plain C, FP64, OpenMP; this
+module only compiles them, marshals numpy arrays, and derives a workload's
 geometry from its primary parameters (its own copy of those rules).
 """
 from __future__ import annotations
@@ -21,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "katsevich_oracle.c")
+_SRC_SIM = os.path.join(_HERE, "simulate_oracle.c")
 _HDR = os.path.join(_HERE, "katsevich_oracle.h")
 
 GEOM_KEYS = ["R", "D", "P", "lambda0", "z0", "lambda_first", "views_per_turn", "n_views",
@@ -43,13 +46,13 @@ class _Geom(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc -O2, OpenMP, no fast-math) into oracle/_build/liboracle.so."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_SIM), os.path.getmtime(_HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
-                           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+                           "-fno-fast-math", "-ffp-contract=off", _SRC, _SRC_SIM, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -96,6 +99,14 @@ def _load():
         "or_filter_adjoint": (None, [_PG, _PI32, _PD, _PI32, _PD, _PD, _I64, _PD]),
         "or_extents": (None, [_PG, _PI32, _PI32, _PD, _PD, _PD]),
         "or_update_count": (_I64, [_PG, _PI32, _PI32]),
+        "or_ray": (None, [_PG, _I64, _I64, _I64, _PD, _PD]),
+        "or_project": (None, [_PG, _PD, _I64, _I64, _PD]),
+        "or_sparse_upsample": (None, [_PG, _PD, _I64, _I64, _PD]),
+        "or_philox4x32_10": (None, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                    ctypes.POINTER(ctypes.c_uint32)]),
+        "or_poisson": (_I64, [_D, ctypes.c_uint64, _I64]),
+        "or_gaussian": (_D, [ctypes.c_uint64, _I64]),
+        "or_add_noise": (None, [_PD, _I64, _D, _D, _D, ctypes.c_uint64, _PD, _PI64, _PD]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -385,3 +396,56 @@ def backproject_points(geom, gF, gf_v0, ijk, windows=None):
     if rc != 0:
         raise ValueError("filtered views do not cover a sampled voxel's PI window")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Data simulation (the paper's Sec. III-C data generation)
+# ---------------------------------------------------------------------------
+def ray(geom, k, r, c):
+    """Source point a and direction d (a + d is the detector sample) of view k, row r, column c."""
+    a, d = np.zeros(3), np.zeros(3)
+    _load().or_ray(ctypes.byref(_g(geom)), k, r, c, _p(a), _p(d))
+    return a, d
+
+
+def project(geom, vol, v0=0, nv=None):
+    """Line integrals of the voxel function (cubes of constant value) for views v0 .. v0+nv-1."""
+    nv = geom["n_views"] - v0 if nv is None else nv
+    f = _f64(vol)
+    out = np.empty((nv, geom["n_rows"], geom["n_cols"]))
+    _load().or_project(ctypes.byref(_g(geom)), _p(f), v0, nv, _p(out))
+    return out
+
+
+def sparse_upsample(geom, sino, keep):
+    """Keep every keep-th detector column, interpolate linearly back to all columns."""
+    s = _f64(sino)
+    out = np.empty_like(s)
+    _load().or_sparse_upsample(ctypes.byref(_g(geom)), _p(s), s.shape[0], keep, _p(out))
+    return out
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    _load().or_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def poisson(lam, seed, i):
+    return _load().or_poisson(lam, seed, i)
+
+
+def gaussian(seed, i):
+    return _load().or_gaussian(seed, i)
+
+
+def add_noise(g_up, I0=1e5, mean=0.0, var=0.5, seed=0):
+    """(g_in, Poisson counts, M) of the Gaussian+Poisson model applied to g_up."""
+    a = _f64(g_up)
+    out = np.empty_like(a)
+    counts = np.empty(a.shape, np.int64)
+    M = ctypes.c_double()
+    _load().or_add_noise(_p(a), a.size, I0, mean, var, seed, _p(out), _p(counts), ctypes.byref(M))
+    return out, counts, M.value

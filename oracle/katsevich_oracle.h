@@ -82,4 +82,14 @@ void or_filter_adjoint(const or_geom *g, const int32_t *kidx, const double *kfra
 void or_extents(const or_geom *g, const int32_t *k0, const int32_t *k1,
                 const double *lam_i, const double *lam_o, double out[6]);
 int64_t or_update_count(const or_geom *g, const int32_t *k0, const int32_t *k1);
+/* data simulation (simulate_oracle.c): the paper's Sec. III-C data generation */
+void or_ray(const or_geom *g, int64_t k, int64_t r, int64_t c, double *a, double *d);
+void or_project(const or_geom *g, const double *vol, int64_t v0, int64_t nv, double *sino);
+void or_sparse_upsample(const or_geom *g, const double *sino, int64_t nv, int64_t keep, double *out);
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+int64_t or_poisson(double lam, uint64_t seed, int64_t i);
+double or_gaussian(uint64_t seed, int64_t i);
+void or_add_noise(const double *g_up, int64_t n, double I0, double mean, double var, uint64_t seed,
+                  double *g_in, int64_t *counts, double *M_out);
+
 #endif
