@@ -339,6 +339,42 @@ KATS_API int64_t katsevich_arena_in_use(const kats_arena *a);
 KATS_API void katsevich_arena_destroy(kats_arena *a);
 
 /*
+ * Data simulation (the paper's Sec. III-C data generation), producing the
+ * network's input sinograms from label volumes.  Conventions and layouts as
+ * above; all pointers are device pointers unless named host_.
+ *
+ * katsevich_project: sino[v - v0][row][col] for views v0 .. v0+nv-1 = the line
+ *   integral, along the ray from the source a(l_v) through the detector sample
+ *   (alpha_col, w_row), of the piecewise-constant voxel function (voxel
+ *   (i, j, s) is the cube of side dx, dy, dz centred at (x0 + i dx, y0 + j dy,
+ *   z_first + s dz) with value vol[s][j][i]; zero outside the volume).  Only
+ *   the geometry's scan and volume fields are used (P, not a plan); the volume
+ *   must hold fewer than 2^31 voxels.
+ * katsevich_sparse_upsample: the sparse detector (columns 0, keep, 2 keep, ...
+ *   of each row of nv views) interpolated linearly back to every column;
+ *   columns past the last kept one take its value.  sino and out must not
+ *   overlap.
+ * katsevich_add_noise: M = max(g_up) (of the non-negative entries, 0 if none),
+ *   counts_i = Poisson(I0 exp(-g_up_i / M)) (a draw of the generator
+ *   Philox4x32-10 keyed by seed with counter (i, draw, 0): PTRS transformed
+ *   rejection for means >= 10, multiplication of uniforms below), plus
+ *   mean + sqrt(var) z_i with z_i normal (Box-Muller on counter (i, 0, 1)),
+ *   floored at 1; g_in_i = M log(I0 / that).  The paper's "g + poisson(g)" is
+ *   read as the Poisson draw of g.  counts (nullable, int64) receives the
+ *   Poisson draws.  workspace holds katsevich_noise_workspace_bytes() bytes;
+ *   host_M (nullable) receives M and makes the call synchronous.  The result
+ *   depends only on (g_up, I0, mean, var, seed), not on launch shape.
+ */
+KATS_API int katsevich_project(const kats_geometry *g, const float *vol, float *sino, int64_t v0, int64_t nv,
+                               void *stream);
+KATS_API int katsevich_sparse_upsample(const kats_geometry *g, const float *sino, float *out, int64_t nv, int keep,
+                                       void *stream);
+KATS_API int64_t katsevich_noise_workspace_bytes(void);
+KATS_API int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, double I0, double mean, double var,
+                                 uint64_t seed, int64_t *counts, void *workspace, size_t workspace_bytes,
+                                 double *host_M, void *stream);
+
+/*
  * Host-side fault injection for tests: the next n device allocations the
  * library makes (plan tables and scratch, a server's arena) fail as if the
  * device were out of memory, without calling CUDA; the call then returns

@@ -206,3 +206,52 @@ def pi_endpoints(geom: dict, xyz: np.ndarray):
     lo = np.empty(p.shape[0])
     native.katsevich_pi_endpoints(geom, p.shape[0], p.ctypes.data, li.ctypes.data, lo.ctypes.data)
     return li, lo
+
+
+# --- data simulation (the paper's Sec. III-C data generation) ---------------------
+def project(geom: dict, vol, v0: int = 0, nv: int | None = None, stream=None):
+    """Helical projection of a float32 CUDA volume [nz][ny][nx]: line integrals of
+    the voxel function for views v0 .. v0+nv-1 -> [nv][n_rows][n_cols]."""
+    torch = _torch()
+    nv = geom["n_views"] - v0 if nv is None else nv
+    if vol.dtype != torch.float32 or not vol.is_cuda or not vol.is_contiguous() or \
+            tuple(vol.shape) != (geom["nz"], geom["ny"], geom["nx"]):
+        raise ValueError("expected a contiguous float32 CUDA volume [nz][ny][nx]")
+    out = torch.empty((nv, geom["n_rows"], geom["n_cols"]), dtype=torch.float32, device=vol.device)
+    native.katsevich_project(geom, vol.data_ptr(), out.data_ptr(), v0, nv, _stream_ptr(stream))
+    return out
+
+
+def sparse_upsample(geom: dict, sino, keep: int = 4, stream=None):
+    """Keep every keep-th detector column, interpolate linearly back to all columns."""
+    torch = _torch()
+    if sino.dtype != torch.float32 or not sino.is_cuda or not sino.is_contiguous() or sino.shape[-1] != geom["n_cols"]:
+        raise ValueError("expected a contiguous float32 CUDA sinogram [views][n_rows][n_cols]")
+    out = torch.empty_like(sino)
+    native.katsevich_sparse_upsample(geom, sino.data_ptr(), out.data_ptr(), sino.numel() // (geom["n_rows"] *
+                                     geom["n_cols"]), keep, _stream_ptr(stream))
+    return out
+
+
+def add_noise(g_up, I0: float = 1e5, mean: float = 0.0, var: float = 0.5, seed: int = 0, return_counts=False,
+              stream=None):
+    """Gaussian+Poisson noise of the paper's data generation: (g_in, M[, counts])."""
+    torch = _torch()
+    if g_up.dtype != torch.float32 or not g_up.is_cuda or not g_up.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    out = torch.empty_like(g_up)
+    counts = torch.empty(g_up.shape, dtype=torch.int64, device=g_up.device) if return_counts else None
+    ws = torch.empty(native.katsevich_noise_workspace_bytes(), dtype=torch.uint8, device=g_up.device)
+    M = native.katsevich_add_noise(g_up.data_ptr(), out.data_ptr(), g_up.numel(), I0, mean, var, seed,
+                                   counts.data_ptr() if counts is not None else None, ws.data_ptr(), ws.numel(),
+                                   _stream_ptr(stream))
+    return (out, M, counts) if return_counts else (out, M)
+
+
+def simulate_input(geom: dict, vol, keep: int = 4, I0: float = 1e5, var: float = 0.5, seed: int = 0, stream=None):
+    """The network input of the paper's data generation: project the label
+    volume, keep every keep-th column and upsample, add Gaussian+Poisson noise."""
+    g_gt = project(geom, vol, stream=stream)
+    g_up = sparse_upsample(geom, g_gt, keep, stream=stream) if keep > 1 else g_gt
+    g_in, _ = add_noise(g_up, I0=I0, var=var, seed=seed, stream=stream)
+    return g_gt, g_in

@@ -13,6 +13,9 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libkatsevich.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# simulate.cu: no contraction of multiply-adds, so the FP64 steps that decide a
+# random draw round exactly as written (and as the FP64 reference computes them)
+EXTRA = {"simulate.cu": ["-fmad=false"]}
 
 
 def sources():
@@ -41,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-               "-Xptxas", "-v" if verbose else "-O3", "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+               "-Xptxas", "-v" if verbose else "-O3", *EXTRA.get(os.path.basename(src), []),
+               "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         subprocess.check_call(cmd)
         objs.append(obj)
     tmp = LIB + f".tmp{os.getpid()}"

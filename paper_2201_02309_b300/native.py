@@ -25,7 +25,8 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_server_wait", "katsevich_server_stats", "katsevich_server_destroy",
            "katsevich_arena_create", "katsevich_arena_alloc", "katsevich_arena_free",
            "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
-           "katsevich_debug_fail_allocs"]
+           "katsevich_debug_fail_allocs", "katsevich_project", "katsevich_sparse_upsample",
+           "katsevich_noise_workspace_bytes", "katsevich_add_noise"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -123,6 +124,14 @@ def load() -> ctypes.CDLL:
         "katsevich_arena_in_use": (ctypes.c_int64, [P]),
         "katsevich_arena_destroy": (None, [P]),
         "katsevich_debug_fail_allocs": (None, [ctypes.c_int]),
+        "katsevich_project": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64, ctypes.c_int64,
+                                             P]),
+        "katsevich_sparse_upsample": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64,
+                                                     ctypes.c_int, P]),
+        "katsevich_noise_workspace_bytes": (ctypes.c_int64, []),
+        "katsevich_add_noise": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_uint64, P, P, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,3 +306,26 @@ def katsevich_arena_destroy(arena: int) -> None:
 
 def katsevich_debug_fail_allocs(n: int) -> None:
     load().katsevich_debug_fail_allocs(n)
+
+
+# --- data simulation -----------------------------------------------------------
+def katsevich_project(geom: dict, vol_ptr: int, sino_ptr: int, v0: int, nv: int, stream_ptr) -> None:
+    g = geometry_struct(geom)
+    check(load().katsevich_project(ctypes.byref(g), vol_ptr, sino_ptr, v0, nv, stream_ptr))
+
+
+def katsevich_sparse_upsample(geom: dict, sino_ptr: int, out_ptr: int, nv: int, keep: int, stream_ptr) -> None:
+    g = geometry_struct(geom)
+    check(load().katsevich_sparse_upsample(ctypes.byref(g), sino_ptr, out_ptr, nv, keep, stream_ptr))
+
+
+def katsevich_noise_workspace_bytes() -> int:
+    return load().katsevich_noise_workspace_bytes()
+
+
+def katsevich_add_noise(g_up_ptr, g_in_ptr, n, I0, mean, var, seed, counts_ptr, ws_ptr, ws_bytes, stream_ptr,
+                        want_M: bool = True):
+    M = ctypes.c_double()
+    check(load().katsevich_add_noise(g_up_ptr, g_in_ptr, n, I0, mean, var, seed, counts_ptr, ws_ptr, ws_bytes,
+                                     ctypes.byref(M) if want_M else None, stream_ptr))
+    return M.value if want_M else None
