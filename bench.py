@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
     ap.add_argument("--turns", type=int, default=None, help="fewer helix turns (profiling captures only)")
+    ap.add_argument("--simulate", action="store_true", help="time the data-simulation pipeline instead")
     ap.add_argument("--requests", type=int, default=256, help="config 5: requests in the stream")
     ap.add_argument("--slots", type=int, default=4, help="config 5: concurrent requests (CUDA streams)")
     ap.add_argument("--arena-gb", type=float, default=24.0, help="config 5: device arena for running requests")
@@ -510,10 +511,61 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------- data simulation
+def run_simulate(args):
+    """The paper's data generation on the clinical geometry (config 2): helical
+    projection of a 512 x 512 x 256 label volume (all 9280 views), sparse
+    detector (every 4th column) upsampled back, Gaussian+Poisson noise
+    (I0 = 1e5, var = 0.5).  One step = one input sinogram."""
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    import synth
+    from paper_2201_02309_b300 import build
+    build.build()
+    cfg = synth.config(2)
+    g = kats.make_geometry(cfg)
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev).manual_seed(2)
+    vol = torch.rand((g["nz"], g["ny"], g["nx"]), generator=gen, device=dev)
+    rays = g["n_views"] * g["n_rows"] * g["n_cols"]
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        kats.simulate_input(g, vol, keep=4, seed=1)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    for i in range(args.steps):
+        ev[4 * i].record(st)
+        g_gt = kats.project(g, vol)
+        ev[4 * i + 1].record(st)
+        g_up = kats.sparse_upsample(g, g_gt, 4)
+        ev[4 * i + 2].record(st)
+        kats.add_noise(g_up, I0=1e5, var=0.5, seed=i)
+        ev[4 * i + 3].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_proj = statistics.mean(ev[4 * i].elapsed_time(ev[4 * i + 1]) for i in range(args.steps))
+    t_up = statistics.mean(ev[4 * i + 1].elapsed_time(ev[4 * i + 2]) for i in range(args.steps))
+    t_noise = statistics.mean(ev[4 * i + 2].elapsed_time(ev[4 * i + 3]) for i in range(args.steps))
+    total = t_proj + t_up + t_noise
+    line = {"metric": "data simulation rays/s (projection + sparse upsampling + noise)", "value": rays / total * 1e3,
+            "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (noise decisions f64)",
+            "data": "synthetic", "config": {"workload": "simulate_det64x736_vol512x512x256_views9280",
+                                            "keep": 4, "I0": 1e5, "var": 0.5},
+            "stages_ms": {"project": t_proj, "sparse_upsample": t_up, "noise": t_noise},
+            "gpu_launches": 4 * args.steps, "clocks": clk}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.simulate:
+        run_simulate(args)
     elif args.config == 5:
         run_serving(args)
     else:

@@ -804,12 +804,270 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
     }
 }
 
+// Transpose of step 7 with a shared-memory window per view: a CTA of 16 x 16
+// voxel columns x 16 slices adds its four bilinear taps per (voxel, view) into
+// the view's detector window in shared memory (the window the forward kernel
+// stages), then adds the window's non-zero entries to g^F with one global
+// atomic each.  The window holds fixed point in two 32-bit integer planes
+// (native integer shared atomics; float and 64-bit ones are compare-and-swap
+// loops, 8-10 times slower here): each CTA scales by a power of two 2^s chosen
+// from its largest possible contribution c_max < 2^e, s = 18 - e; a
+// contribution x adds h = round(x 2^s) to the high plane and
+// round((x 2^s - h) 2^12) to the low plane.  One window entry takes at most
+// 4096 contributions, so the planes stay below 2^30 and 2^23, and the
+// quantum is 2^-30 c_max.  Two windows alternate (one filling,
+// one draining), one CTA barrier per view; the window's first column per view
+// is computed at the tile corners one view ahead.
+constexpr int BT_THREADS = B2_TX * B2_TY;
+
+// x (already scaled, |x| < 2^18, or the sum of at most three such on one
+// row of one thread) into the high plane at p and its rounding remainder,
+// times 2^12, into the low plane at p + plane.
+__device__ __forceinline__ void deposit(int *p, int plane, float x)
+{
+    const int h = __float2int_rn(x);
+    atomicAdd(p, h);
+    atomicAdd(p + plane, __float2int_rn((x - (float)h) * 4096.0f));
+}
+
+template <int PITCH, bool POLY, bool ROWS_OK>
+__global__ void __launch_bounds__(BT_THREADS, 2)
+    k_backproject_T_win(BPArgs a, int W, int srows, int slot_floats, float out_scale, float inv_v_max,
+                        const float *__restrict__ vol, float *gF)
+{
+    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
+    extern __shared__ int win[];  // [2 windows][2 planes][slot_floats] fixed-point sums
+    __shared__ int s_col[3];
+    __shared__ int s_K0, s_K1;
+    __shared__ float s_fmax[BT_THREADS / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx = tid % B2_TX, ty = tid / B2_TX;
+    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    const int s0 = blockIdx.z * B2_T;
+    const bool active = ix < a.nx && iy < a.ny;
+
+    int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
+    float lo[B2_T], hi[B2_T], f[B2_T];
+    {
+        int ka[B2_T], kb[B2_T];
+        float wa[B2_T], wb[B2_T];
+#pragma unroll
+        for (int t = 0; t < B2_T; ++t) {
+            const int s = s0 + t;
+            ka[t] = INT32_MAX;
+            kb[t] = INT32_MIN;
+            wa[t] = wb[t] = f[t] = 0.0f;
+            if (active && s < a.nz) {
+                const int j = s % a.N, m = s / a.N;
+                const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
+                ka[t] = a.k0[o] + m * a.vpt;
+                kb[t] = a.k1[o] + m * a.vpt;
+                wa[t] = a.w0[o];
+                wb[t] = a.w1[o];
+                f[t] = vol[((int64_t)s * a.ny + iy) * a.nx + ix] * out_scale;
+                if (ka[t] <= kb[t]) {
+                    kmin = min(kmin, ka[t]);
+                    kmax = max(kmax, kb[t]);
+                }
+            }
+            kfull_lo = max(kfull_lo, ka[t]);
+            kfull_hi = min(kfull_hi, kb[t]);
+        }
+        const int kbase = kmin <= kmax ? kmin : 0;
+#pragma unroll
+        for (int t = 0; t < B2_T; ++t) {
+            if (ka[t] <= kb[t]) {
+                lo[t] = (float)(ka[t] - kbase) - wa[t];
+                hi[t] = (float)(kb[t] - kbase) + wb[t];
+            } else {
+                lo[t] = 3.0e9f;
+                hi[t] = -3.0e9f;
+            }
+        }
+    }
+    if (tid == 0) {
+        s_K0 = INT32_MAX;
+        s_K1 = INT32_MIN;
+    }
+    float fm = 0.0f;
+#pragma unroll
+    for (int t = 0; t < B2_T; ++t) fm = fmaxf(fm, fabsf(f[t]));
+    for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+    if (lane == 0) s_fmax[warp] = fm;
+    for (int e = tid; e < 4 * slot_floats; e += BT_THREADS) win[e] = 0;
+    __syncthreads();
+    // fixed-point scale: 2^(18 - e) with the largest contribution below 2^e
+    fm = 0.0f;
+    for (int w8 = 0; w8 < BT_THREADS / 32; ++w8) fm = fmaxf(fm, s_fmax[w8]);
+    int ex = 0;
+    frexpf(fm * inv_v_max, &ex);
+    const float scale = fm > 0.0f ? exp2f((float)min(18 - ex, 126)) : 0.0f;
+    const float inv_scale = fm > 0.0f ? exp2f(-(float)min(18 - ex, 126)) : 0.0f;
+    if (kmin <= kmax) {
+        atomicMin(&s_K0, kmin);
+        atomicMax(&s_K1, kmax);
+    }
+    __syncthreads();
+    const int K0 = s_K0, K1 = s_K1;
+    if (K0 > K1) return;  // uniform: no voxel of the tile has a PI view
+    const int nviews = K1 - K0 + 1;
+
+    // first window column of view k: lowest column touched at the tile corners, one column of slack
+    const int ixa = blockIdx.x * B2_TX, iya = blockIdx.y * B2_TY;
+    const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
+    const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
+    auto window_col = [&](int k) {
+        const int km = ((k % a.vpt) + a.vpt) % a.vpt;
+        const float2 cs = __ldg(a.trig + km);
+        const float v = a.R - cx * cs.x - cy * cs.y;
+        const float u = -cx * cs.y + cy * cs.x;
+        float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
+        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
+        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
+        return ((int)floorf(c) - 1) & ~3;
+    };
+    if (warp == 0) {
+        const int c = window_col(K0);
+        if (lane == 0) s_col[0] = c;
+    }
+    __syncthreads();
+
+    const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
+    const int kbase = kmin <= kmax ? kmin : 0;
+    float zb, zb_lo;
+    z_base(a, s0, kbase, &zb, &zb_lo);
+    const float rmax = (float)(a.n_rows + 1);
+    const int64_t per_view = (int64_t)a.n_rows * a.gcols;
+    const int wsize = srows * PITCH;
+    int km = ((K0 % a.vpt) + a.vpt) % a.vpt;
+    for (int j = 0; j < nviews; ++j) {
+        const int k = K0 + j;
+        const int b = j & 1;
+        if (warp == 0 && j + 1 < nviews) {
+            const int c = window_col(k + 1);
+            if (lane == 0) s_col[(j + 1) % 3] = c;
+        }
+        if (active && k >= kmin && k <= kmax) {
+            const float2 cs = __ldg(a.trig + km);
+            const float v = fmaf(-x, cs.x, fmaf(-y, cs.y, a.R));
+            const float u = fmaf(-x, cs.y, y * cs.x);
+            const float inv_v = rcp_approx(v);
+            int ci;
+            float fc;
+            column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
+            const uint32_t colx = (uint32_t)(2 * b * slot_floats + min(max(ci - s_col[j % 3], 0), W - 2)) -
+                                  (0x4B000000u << SH);
+            const float M = a.D * rsqrtf(fmaf(u, u, v * v));
+            const float kf = (float)(k - kbase);
+            const float ur0 = (M * z_rel(a, zb, zb_lo, kf) - a.w0row) * a.inv_dw + 1.0f;
+            const float dur = M * a.dz_over_dw;
+            const bool full = k > kfull_lo && k < kfull_hi;
+            // The slices' rows rise with t (dur > 0), so a thread's taps of one view fall
+            // on a run of rows of two columns: sum them per row in registers (rows qa and
+            // qa + PITCH pending) and deposit a row once the run has moved past it.
+            constexpr uint32_t kNone = 0xFFFFFFFFu;
+            uint32_t qa = kNone;  // window offset of the pending top row
+            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;  // pending rows, columns ci and ci + 1
+#pragma unroll
+            for (int t = 0; t < B2_T; ++t) {
+                const float om = full ? 1.0f : __saturatef(kf - lo[t]) * __saturatef(hi[t] - kf);
+                const float wv = om * inv_v * f[t];
+                if (wv == 0.0f) continue;
+                float ur = fmaf((float)t, dur, ur0);
+                if (!ROWS_OK) ur = fminf(fmaxf(ur, 0.0f), rmax);
+                const float yv = __fadd_rd(ur, 8388608.0f);
+                const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
+                const float fr = ur - (yv - 8388608.0f);
+                const float top = wv * scale * (1.0f - fr), bot = wv * scale * fr;
+                if (q != qa) {
+                    if (qa != kNone) {
+                        deposit(win + qa, slot_floats, a0);
+                        deposit(win + qa + 1, slot_floats, a1);
+                    }
+                    if (qa != kNone && q == qa + PITCH) {  // down one row: the old bottom row becomes the top
+                        a0 = b0;
+                        a1 = b1;
+                    } else {
+                        if (qa != kNone) {
+                            deposit(win + qa + PITCH, slot_floats, b0);
+                            deposit(win + qa + PITCH + 1, slot_floats, b1);
+                        }
+                        a0 = a1 = 0.0f;
+                    }
+                    b0 = b1 = 0.0f;
+                    qa = q;
+                }
+                a0 = fmaf(top, 1.0f - fc, a0);
+                a1 = fmaf(top, fc, a1);
+                b0 = fmaf(bot, 1.0f - fc, b0);
+                b1 = fmaf(bot, fc, b1);
+            }
+            if (qa != kNone) {
+                deposit(win + qa, slot_floats, a0);
+                deposit(win + qa + 1, slot_floats, a1);
+                deposit(win + qa + PITCH, slot_floats, b0);
+                deposit(win + qa + PITCH + 1, slot_floats, b1);
+            }
+        }
+        if (++km == a.vpt) km = 0;
+        __syncthreads();  // window b of view k is complete; window b^1 (view k-1) has been drained
+        // drain window b into g^F: staged row 0 is detector row -1, columns from s_col
+        const int col0 = s_col[j % 3];
+        int *w = win + 2 * b * slot_floats;
+        float *view = gF + (int64_t)(k - a.first_view) * per_view;
+        for (int e = tid; e < wsize; e += BT_THREADS) {
+            const int hi = w[e], lo = w[e + slot_floats];
+            if ((hi | lo) == 0) continue;
+            w[e] = 0;
+            w[e + slot_floats] = 0;
+            const int r = e / PITCH - 1, c = col0 + e % PITCH;
+            if (r >= 0 && r < a.n_rows && c >= 0 && c < a.n_cols)
+                atomicAdd(view + r * a.gcols + c, fmaf((float)lo, 1.0f / 4096.0f, (float)hi) * inv_scale);
+        }
+    }
+}
+
+template <int PITCH>
+static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, float *gF, int W, cudaStream_t st,
+                              bool *launched)
+{
+    *launched = false;
+    const int srows = (int)p.g.n_rows + 3;
+    const int slot = (PITCH * srows + 31) / 32 * 32;
+    const size_t smem = sizeof(int) * (size_t)slot * 4;
+    if (W > PITCH || smem > 100 * 1024 || p.n_fviews >= INT32_MAX || !(p.g.R > p.r_fov)) return KATS_OK;
+    const bool poly = p.r_fov <= p.g.R * 0.70710678;
+    const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
+    const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
+    const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
+    auto kern = poly ? (rows_ok ? k_backproject_T_win<PITCH, true, true> : k_backproject_T_win<PITCH, true, false>)
+                     : (rows_ok ? k_backproject_T_win<PITCH, false, true> : k_backproject_T_win<PITCH, false, false>);
+    KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY), (unsigned)ceil_div(p.g.nz, B2_T));
+    // 1/v* <= 1/(R - r_fov) for every voxel column, rounded up
+    const float inv_v_max = (float)(1.0 / (p.g.R - p.r_fov)) * 1.0001f;
+    kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, vol, gF);
+    KATS_CUDA(cudaGetLastError());
+    *launched = true;
+    return KATS_OK;
+}
+
 int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaStream_t st)
 {
     BPArgs a = bp_args(p);
     a.gF = gF;
     a.vol = nullptr;
     KATS_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols), st));
+    const int W = window_cols(p);
+    bool launched = false;
+    int rc = KATS_OK;
+    if (W <= 32)
+        rc = launch_adjoint_win<32>(p, a, vol, gF, W, st, &launched);
+    else if (W <= 64)
+        rc = launch_adjoint_win<64>(p, a, vol, gF, W, st, &launched);
+    else if (W <= 128)
+        rc = launch_adjoint_win<128>(p, a, vol, gF, W, st, &launched);
+    if (rc || launched) return rc;
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
     k_backproject_T<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a, vol, gF);
     KATS_CUDA(cudaGetLastError());
