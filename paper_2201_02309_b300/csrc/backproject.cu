@@ -311,10 +311,10 @@ __device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float 
     for (int pr = 0; pr < B2_T / 2; ++pr) {
         const float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
         if (WEIGHTED) {
-            const float om0 = __saturatef(kf - lo[2 * pr]) * __saturatef(hi[2 * pr] - kf);
-            const float om1 = __saturatef(kf - lo[2 * pr + 1]) * __saturatef(hi[2 * pr + 1] - kf);
-            if (om0 == 0.0f && om1 == 0.0f) continue;
-            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, make_float2(om0 * inv_v, om1 * inv_v),
+            const float2 om = __fmul2_rn(make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1])),
+                                         make_float2(__saturatef(hi[2 * pr] - kf), __saturatef(hi[2 * pr + 1] - kf)));
+            if (om.x == 0.0f && om.y == 0.0f) continue;
+            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, __fmul2_rn(om, make_float2(inv_v, inv_v)),
                                        acc2[pr]);
         } else {
             bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), acc2[pr]);
