@@ -1,6 +1,7 @@
 // C-ABI entry points of the reconstruction step (Sec. II): steps 1-6 then 7,
 // their transposes, and the host-buffer variant.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -84,18 +85,72 @@ size_t host_item_bytes(const Plan &p, int precision)
 
 // One item from host buffers, stream-ordered and asynchronous: copy the view
 // window the volume needs, steps 1-7, copy the volume back.  ws holds
-// host_item_bytes(p, precision) bytes.
+// host_item_bytes(p, precision) bytes.  The copies overlap the kernels: the
+// window arrives in chunks on a second stream while earlier chunks are
+// filtered, and the volume leaves in slabs of slices while later slabs are
+// backprojected.  Work issued on st after this call waits for all of it.
 int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
 {
-    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view_elems(p);
+    const size_t view = view_elems(p);
+    const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view;
     float *d_win = (float *)ws;
     float *d_vol = (float *)((char *)ws + align256(win));
     char *rws = (char *)d_vol + align256(sizeof(float) * vol_item(p));
-    KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + p.first_view * view_elems(p), win, cudaMemcpyHostToDevice, st));
-    int rc = recon_item(p, precision, d_win, d_vol, rws, recon_ws_for(p, precision), st);
-    if (rc) return rc;
-    KATS_CUDA(cudaMemcpyAsync(host_vol, d_vol, sizeof(float) * vol_item(p), cudaMemcpyDeviceToHost, st));
-    return KATS_OK;
+    const bool fp32 = precision == KATS_PREC_FP32;
+    const size_t gfb = fp32 ? align256(gf_bytes(p)) : align256(gfp_bytes(p));
+    char *fws = rws + gfb;
+    const size_t fws_bytes = recon_ws_for(p, precision) - gfb;
+    const int64_t nf = p.n_fviews, nz = p.g.nz, nxy = p.g.nx * p.g.ny;
+    const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(8, nf / 256));
+    const int slab = (int)std::max<int64_t>(16, ((nz + 3) / 4 + 15) / 16 * 16);  // about 4 slabs of whole z tiles
+    const int n_slabs = (int)((nz + slab - 1) / slab);
+
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)(n_chunks + n_slabs + 2), nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);  // released once recorded work completes
+        if (cs) cudaStreamDestroy(cs);   // likewise
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (size_t i = 0; e == cudaSuccess && i < ev.size(); ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    int rc = KATS_OK;
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy stream and events");
+    // the copy stream starts after the work already issued on st (e.g. a previous item using ws)
+    if (!rc && (e = cudaEventRecord(ev[0], st)) == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+    for (int i = 0; !rc && e == cudaSuccess && i < n_chunks; ++i) {
+        const int64_t v0 = nf * i / n_chunks, v1 = nf * (i + 1) / n_chunks;  // filtered views [v0, v1) need [v0, v1]
+        e = cudaMemcpyAsync(d_win + v0 * view, host_sino + (p.first_view + v0) * view,
+                            sizeof(float) * (size_t)(v1 - v0 + 1) * view, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], cs);
+    }
+    for (int i = 0; !rc && e == cudaSuccess && i < n_chunks; ++i) {
+        const int64_t v0 = nf * i / n_chunks, v1 = nf * (i + 1) / n_chunks;
+        e = cudaStreamWaitEvent(st, ev[1 + i], 0);
+        if (e != cudaSuccess) break;
+        if (fp32)
+            rc = launch_filter(p, d_win + v0 * view, (float *)rws + v0 * p.g.n_rows * p.gf_cols, fws, fws_bytes, st,
+                               v1 - v0);
+        else
+            rc = launch_filter16(p, precision, d_win + v0 * view,
+                                 (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, st, v1 - v0);
+    }
+    for (int j = 0; !rc && e == cudaSuccess && j < n_slabs; ++j) {
+        const int s0 = j * slab, n = (int)std::min<int64_t>(slab, nz - s0);
+        rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
+                  : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
+        if (rc) break;
+        e = cudaEventRecord(ev[1 + n_chunks + j], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[1 + n_chunks + j], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_vol + s0 * nxy, d_vol + s0 * nxy, sizeof(float) * (size_t)(n * nxy),
+                                cudaMemcpyDeviceToHost, cs);
+    }
+    if (!rc && e == cudaSuccess && (e = cudaEventRecord(ev[ev.size() - 1], cs)) == cudaSuccess)
+        e = cudaStreamWaitEvent(st, ev[ev.size() - 1], 0);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "pipelined host item");
+    cleanup();
+    return rc;
 }
 
 }  // namespace kats

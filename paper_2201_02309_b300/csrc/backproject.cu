@@ -38,6 +38,7 @@ struct BPArgs {
     const float *w0, *w1;
     const float2 *trig, *trig_lo;
     int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
+    int s_begin, s_end;  // slices [s_begin, s_end) of this launch; s_begin a multiple of the z tile
     int64_t first_view;
     float R, D, x0, y0, dx, dy;
     float alpha0, inv_da, w0row, inv_dw, dz_over_dw, scale;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 {
     const int ix = blockIdx.x * BP_BX + threadIdx.x;
     const int iy = blockIdx.y * BP_BY + threadIdx.y;
-    const int s0 = blockIdx.z * BP_T;
+    const int s0 = a.s_begin + blockIdx.z * BP_T;
     if (ix >= a.nx || iy >= a.ny) return;
     int ka[BP_T], kb[BP_T];
     float wa[BP_T], wb[BP_T], acc[BP_T];
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     for (int t = 0; t < BP_T; ++t) {
         acc[t] = 0.0f;
         const int s = s0 + t;
-        if (s < a.nz) {
+        if (s < a.s_end) {
             const int j = s % a.N, m = s / a.N;
             const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
             ka[t] = a.k0[o] + m * a.vpt;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 #pragma unroll
     for (int t = 0; t < BP_T; ++t) {
         const int s = s0 + t;
-        if (s < a.nz) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = acc[t] * a.scale;
+        if (s < a.s_end) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = acc[t] * a.scale;
     }
 }
 
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const bool producer = warp == B2_CW;
     const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
     const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
-    const int s0 = blockIdx.z * B2_T;
+    const int s0 = a.s_begin + blockIdx.z * B2_T;
     const bool active = !producer && ix < a.nx && iy < a.ny;
     // slots start at the first 128-byte boundary of the dynamic shared memory (TMA destinations)
     const int base = (int)(((128u - (smem_addr(smem) & 127u)) & 127u) >> 2);
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             ka[t] = INT32_MAX;
             kb[t] = INT32_MIN;
             wa[t] = wb[t] = 0.0f;
-            if (active && s < a.nz) {
+            if (active && s < a.s_end) {
                 const int j = s % a.N, m = s / a.N;
                 const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
                 ka[t] = a.k0[o] + m * a.vpt;
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
         const int s = s0 + t;
-        if (s < a.nz) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = ((t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x) * p.out_scale;
+        if (s < a.s_end) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = ((t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x) * p.out_scale;
     }
 }
 
@@ -586,6 +587,8 @@ static BPArgs bp_args(const Plan &p)
     a.nx = (int)g.nx;
     a.ny = (int)g.ny;
     a.nz = (int)g.nz;
+    a.s_begin = 0;
+    a.s_end = (int)g.nz;
     a.N = (int)p.N;
     a.vpt = (int)g.views_per_turn;
     a.n_rows = (int)g.n_rows;
@@ -684,7 +687,8 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     auto kern = poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true> : k_backproject_tma<PITCH, MODE, true, false>)
                      : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true> : k_backproject_tma<PITCH, MODE, false, false>);
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY), (unsigned)ceil_div(p.g.nz, B2_T));
+    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
+              (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
     kern<<<grid, B2_THREADS, smem, st>>>(map, b);
     KATS_CUDA(cudaGetLastError());
     *launched = true;
@@ -701,9 +705,14 @@ static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W,
     return KATS_OK;
 }
 
-int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st)
+int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st, int s_begin,
+                         int s_count)
 {
     BPArgs a = bp_args(p);
+    if (s_count >= 0) {
+        a.s_begin = s_begin;
+        a.s_end = std::min(s_begin + s_count, (int)p.g.nz);
+    }
     a.gF = nullptr;
     a.vol = vol;
     bool launched = false;
@@ -719,16 +728,21 @@ int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vo
     return KATS_OK;
 }
 
-int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st)
+int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st, int s_begin, int s_count)
 {
     BPArgs a = bp_args(p);
+    if (s_count >= 0) {
+        a.s_begin = s_begin;
+        a.s_end = std::min(s_begin + s_count, (int)p.g.nz);
+    }
     a.gF = gF;
     a.vol = vol;
     const int W = window_cols(p);
     bool launched = false;
     int rc = launch_tma_any<0>(p, a, gF, W, st, &launched);
     if (rc || launched) return rc;
-    dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
+    dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
+              (unsigned)ceil_div(a.s_end - a.s_begin, BP_T));
     k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
@@ -745,7 +759,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
 {
     const int ix = blockIdx.x * BP_BX + threadIdx.x;
     const int iy = blockIdx.y * BP_BY + threadIdx.y;
-    const int s0 = blockIdx.z * BP_T;
+    const int s0 = a.s_begin + blockIdx.z * BP_T;
     if (ix >= a.nx || iy >= a.ny) return;
     int ka[BP_T], kb[BP_T];
     float wa[BP_T], wb[BP_T], f[BP_T];
@@ -753,7 +767,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
 #pragma unroll
     for (int t = 0; t < BP_T; ++t) {
         const int s = s0 + t;
-        if (s < a.nz) {
+        if (s < a.s_end) {
             const int j = s % a.N, m = s / a.N;
             const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
             ka[t] = a.k0[o] + m * a.vpt;
@@ -843,7 +857,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tx = tid % B2_TX, ty = tid / B2_TX;
     const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
-    const int s0 = blockIdx.z * B2_T;
+    const int s0 = a.s_begin + blockIdx.z * B2_T;
     const bool active = ix < a.nx && iy < a.ny;
 
     int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
@@ -857,7 +871,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
             ka[t] = INT32_MAX;
             kb[t] = INT32_MIN;
             wa[t] = wb[t] = f[t] = 0.0f;
-            if (active && s < a.nz) {
+            if (active && s < a.s_end) {
                 const int j = s % a.N, m = s / a.N;
                 const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
                 ka[t] = a.k0[o] + m * a.vpt;
@@ -1043,7 +1057,8 @@ static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, 
     auto kern = poly ? (rows_ok ? k_backproject_T_win<PITCH, true, true> : k_backproject_T_win<PITCH, true, false>)
                      : (rows_ok ? k_backproject_T_win<PITCH, false, true> : k_backproject_T_win<PITCH, false, false>);
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY), (unsigned)ceil_div(p.g.nz, B2_T));
+    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
+              (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
     // 1/v* <= 1/(R - r_fov) for every voxel column, rounded up
     const float inv_v_max = (float)(1.0 / (p.g.R - p.r_fov)) * 1.0001f;
     kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, vol, gF);
@@ -1068,7 +1083,8 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
     else if (W <= 128)
         rc = launch_adjoint_win<128>(p, a, vol, gF, W, st, &launched);
     if (rc || launched) return rc;
-    dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY), (unsigned)ceil_div(p.g.nz, BP_T));
+    dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
+              (unsigned)ceil_div(a.s_end - a.s_begin, BP_T));
     k_backproject_T<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a, vol, gF);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;

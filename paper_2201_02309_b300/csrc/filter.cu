@@ -160,15 +160,17 @@ __global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ 
     }
 }
 
-int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st)
+int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st,
+                  int64_t nv_chunk)
 {
-    const int64_t nv = p.n_fviews, Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
+    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
+    const int64_t Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
     if (ws_bytes < filter_workspace_bytes(p)) {
         set_error("filter workspace too small: %zu < %zu", ws_bytes, filter_workspace_bytes(p));
         return KATS_ESPACE;
     }
     float *g3 = (float *)ws;
-    float *g4 = g3 + nv * np * Kp;
+    float *g4 = g3 + p.n_fviews * np * Kp;  // workspace laid out for every view; a chunk uses the front
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     const size_t smem = sizeof(float) * 32 * (size_t)nr;
     if (smem > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_deriv_rebin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

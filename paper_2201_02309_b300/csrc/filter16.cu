@@ -104,16 +104,18 @@ __global__ void k_unrebin_cos16(const float *__restrict__ g4, uint32_t *__restri
 }
 
 int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
-                    cudaStream_t st)
+                    cudaStream_t st, int64_t nv_chunk)
 {
-    const int64_t nv = p.n_fviews, nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi, M = nv * np;
+    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
+    const int64_t nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi, M = nv * np;
     if (ws_bytes < filter16_workspace_bytes(p)) {
         set_error("filter workspace too small: %zu < %zu", ws_bytes, filter16_workspace_bytes(p));
         return KATS_ESPACE;
     }
     const bool fp16 = prec == KATS_PREC_FP16;
     uint16_t *g3 = (uint16_t *)ws;
-    float *g4 = (float *)((char *)ws + ((size_t)M * (size_t)p.tc_k16 * 2 + 255) / 256 * 256);
+    // workspace laid out for every view; a chunk uses the front of each part
+    float *g4 = (float *)((char *)ws + ((size_t)(p.n_fviews * np) * (size_t)p.tc_k16 * 2 + 255) / 256 * 256);
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     const float scale = (float)p.g.d_alpha;
     const size_t smem = sizeof(float) * 32 * (size_t)nr;

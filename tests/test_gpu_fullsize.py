@@ -79,3 +79,19 @@ def test_c2_voxels_sampled(c2):
     assert kp.info["update_count"] > 4.0e10
     import paper_2201_02309_b300 as kats
     assert kats.native.katsevich_device_status(kp.handle) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_c2_host_pipeline_matches_device(c2, prec):
+    """katsevich_recon_host at full size (8 overlapped window chunks, 4 volume
+    slabs) gives bit for bit the device-buffer result of katsevich_recon."""
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    g, sino, kp, dsino, vol = c2
+    p = {"fp32": kats.KATS_PREC_FP32, "fp16": kats.KATS_PREC_FP16}[prec]
+    dev = vol if prec == "fp32" else kp.recon(dsino, precision=p).cpu().numpy()
+    hs = torch.from_numpy(sino).pin_memory()
+    hv = torch.empty(kp.vol_shape, dtype=torch.float32).pin_memory()
+    kp.recon_host(hs, hv, precision=p)
+    assert np.array_equal(hv.numpy(), dev)
