@@ -83,12 +83,28 @@ size_t host_item_bytes(const Plan &p, int precision)
     return align256(win) + align256(sizeof(float) * vol_item(p)) + recon_ws_for(p, precision);
 }
 
+// Filtered views [lo, hi] (relative to first_view) that slices [s0, s1) read.
+static void slab_views(const Plan &p, int64_t s0, int64_t s1, int64_t *lo, int64_t *hi)
+{
+    int64_t a = INT64_MAX, b = INT64_MIN;
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t j = s % p.N, shift = (s / p.N) * p.g.views_per_turn;
+        if (p.h_slice_kmin[(size_t)j] > p.h_slice_kmax[(size_t)j]) continue;  // no voxel of the slice has a window
+        a = std::min<int64_t>(a, p.h_slice_kmin[(size_t)j] + shift);
+        b = std::max<int64_t>(b, p.h_slice_kmax[(size_t)j] + shift);
+    }
+    *lo = a == INT64_MAX ? 0 : a - p.first_view;
+    *hi = b == INT64_MIN ? -1 : b - p.first_view;
+}
+
 // One item from host buffers, stream-ordered and asynchronous: copy the view
 // window the volume needs, steps 1-7, copy the volume back.  ws holds
 // host_item_bytes(p, precision) bytes.  The copies overlap the kernels: the
-// window arrives in chunks on a second stream while earlier chunks are
-// filtered, and the volume leaves in slabs of slices while later slabs are
-// backprojected.  Work issued on st after this call waits for all of it.
+// window arrives in chunks on a second stream; a slab of slices is
+// backprojected as soon as the chunks holding its views are filtered (the PI
+// windows rise with z), while later chunks are still arriving; each slab of
+// the volume is copied back while later slabs are backprojected.  Work issued
+// on st after this call waits for all of it.
 int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
 {
     const size_t view = view_elems(p);
@@ -101,9 +117,10 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     char *fws = rws + gfb;
     const size_t fws_bytes = recon_ws_for(p, precision) - gfb;
     const int64_t nf = p.n_fviews, nz = p.g.nz, nxy = p.g.nx * p.g.ny;
-    const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(8, nf / 256));
-    const int slab = (int)std::max<int64_t>(16, ((nz + 3) / 4 + 15) / 16 * 16);  // about 4 slabs of whole z tiles
+    const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, nf / 256));
+    const int slab = (int)std::max<int64_t>(16, ((nz + 5) / 6 + 15) / 16 * 16);  // about 6 slabs of whole z tiles
     const int n_slabs = (int)((nz + slab - 1) / slab);
+    auto chunk_lo = [&](int i) { return nf * i / n_chunks; };
 
     cudaStream_t cs = nullptr;
     std::vector<cudaEvent_t> ev((size_t)(n_chunks + n_slabs + 2), nullptr);
@@ -119,24 +136,31 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     // the copy stream starts after the work already issued on st (e.g. a previous item using ws)
     if (!rc && (e = cudaEventRecord(ev[0], st)) == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
     for (int i = 0; !rc && e == cudaSuccess && i < n_chunks; ++i) {
-        const int64_t v0 = nf * i / n_chunks, v1 = nf * (i + 1) / n_chunks;  // filtered views [v0, v1) need [v0, v1]
+        const int64_t v0 = chunk_lo(i), v1 = chunk_lo(i + 1);  // filtered views [v0, v1) need [v0, v1]
         e = cudaMemcpyAsync(d_win + v0 * view, host_sino + (p.first_view + v0) * view,
                             sizeof(float) * (size_t)(v1 - v0 + 1) * view, cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1 + i], cs);
     }
-    for (int i = 0; !rc && e == cudaSuccess && i < n_chunks; ++i) {
-        const int64_t v0 = nf * i / n_chunks, v1 = nf * (i + 1) / n_chunks;
-        e = cudaStreamWaitEvent(st, ev[1 + i], 0);
-        if (e != cudaSuccess) break;
-        if (fp32)
-            rc = launch_filter(p, d_win + v0 * view, (float *)rws + v0 * p.g.n_rows * p.gf_cols, fws, fws_bytes, st,
-                               v1 - v0);
-        else
-            rc = launch_filter16(p, precision, d_win + v0 * view,
-                                 (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, st, v1 - v0);
-    }
+    int filtered = 0;  // chunks already filtered on st
     for (int j = 0; !rc && e == cudaSuccess && j < n_slabs; ++j) {
         const int s0 = j * slab, n = (int)std::min<int64_t>(slab, nz - s0);
+        int64_t lo, hi;
+        slab_views(p, s0, s0 + n, &lo, &hi);
+        // filter every chunk up to the one holding the slab's last view
+        while (!rc && e == cudaSuccess && filtered < n_chunks && (j == n_slabs - 1 || chunk_lo(filtered) <= hi)) {
+            const int i = filtered++;
+            const int64_t v0 = chunk_lo(i), v1 = chunk_lo(i + 1);
+            e = cudaStreamWaitEvent(st, ev[1 + i], 0);
+            if (e != cudaSuccess) break;
+            if (fp32)
+                rc = launch_filter(p, d_win + v0 * view, (float *)rws + v0 * p.g.n_rows * p.gf_cols, fws, fws_bytes,
+                                   st, v1 - v0);
+            else
+                rc = launch_filter16(p, precision, d_win + v0 * view,
+                                     (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, st,
+                                     v1 - v0);
+        }
+        if (rc || e != cudaSuccess) break;
         rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
                   : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
         if (rc) break;

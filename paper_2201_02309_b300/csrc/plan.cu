@@ -668,6 +668,8 @@ static int build(Plan *p)
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "plan kernels and reductions");
 
+    p->h_slice_kmin = kmin;
+    p->h_slice_kmax = kmax;
     // views the whole volume needs; slice s uses table slice s mod N shifted by (s div N) turns
     int64_t vmin = INT64_MAX, vmax = INT64_MIN, count = 0;
     for (int64_t j = 0; j < N && j < g.nz; ++j) {
