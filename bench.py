@@ -511,6 +511,57 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------- differentiation
+def run_differentiation(args):
+    """Config 3: the operator as a differentiable layer.  One step = forward
+    (steps 1-7) and backward (the hand-written adjoint) of a batch of 4
+    sinograms of the sparse-detector scanner (368 columns, 580 views/turn,
+    1.5 x max-fit pitch, 256 x 256 x 64 volume) through torch.autograd."""
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    import synth
+    from paper_2201_02309_b300 import build
+    from paper_2201_02309_b300.autograd import KatsevichLayer
+    build.build()
+    cfg = synth.config(3)
+    g = kats.make_geometry(cfg)
+    layer = KatsevichLayer(g)
+    B = int(cfg["batch"])
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev).manual_seed(3)
+    sino = torch.randn((B,) + layer.plan.sino_shape, generator=gen, device=dev).requires_grad_(True)
+    cot = torch.randn((B,) + layer.plan.vol_shape, generator=gen, device=dev)
+    upd = float(layer.plan.info["update_count"]) * B
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        layer(sino).backward(cot)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    for i in range(args.steps):
+        sino.grad = None
+        ev[3 * i].record(st)
+        vol = layer(sino)
+        ev[3 * i + 1].record(st)
+        vol.backward(cot)
+        ev[3 * i + 2].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd = statistics.mean(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps))
+    bwd = statistics.mean(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps))
+    line = {"metric": METRIC, "value": upd / (fwd + bwd) * 1e-6, "unit": "GUPS (forward + backward updates/s)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd + bwd,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "batch": B, "volume_xyz": [g["nx"], g["ny"], g["nz"]],
+                       "detector_rows_cols": [g["n_rows"], g["n_cols"]], "views_per_turn": g["views_per_turn"],
+                       "pitch_mm": g["P"], "updates_per_volume": upd / B},
+            "forward_ms": fwd, "backward_ms": bwd, "forward_gups": upd / fwd * 1e-6, "backward_gups": upd / bwd * 1e-6,
+            "gpu_launches": None, "clocks": clk}
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------- data simulation
 def run_simulate(args):
     """The paper's data generation on the clinical geometry (config 2): helical
@@ -523,7 +574,7 @@ def run_simulate(args):
     import synth
     from paper_2201_02309_b300 import build
     build.build()
-    cfg = synth.config(2)
+    cfg = config_for(argparse.Namespace(config=2, nz=args.nz, turns=args.turns))
     g = kats.make_geometry(cfg)
     dev = torch.device("cuda:0")
     gen = torch.Generator(device=dev).manual_seed(2)
@@ -553,7 +604,7 @@ def run_simulate(args):
     line = {"metric": "data simulation rays/s (projection + sparse upsampling + noise)", "value": rays / total * 1e3,
             "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (noise decisions f64)",
-            "data": "synthetic", "config": {"workload": "simulate_det64x736_vol512x512x256_views9280",
+            "data": "synthetic", "config": {"workload": "simulate_" + cfg["name"], "views": g["n_views"],
                                             "keep": 4, "I0": 1e5, "var": 0.5},
             "stages_ms": {"project": t_proj, "sparse_upsample": t_up, "noise": t_noise},
             "gpu_launches": 4 * args.steps, "clocks": clk}
@@ -568,6 +619,8 @@ def main():
         run_simulate(args)
     elif args.config == 5:
         run_serving(args)
+    elif args.config == 3:
+        run_differentiation(args)
     else:
         run_ours(args)
 
