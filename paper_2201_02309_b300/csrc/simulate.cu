@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs P, const float *__rest
     const double d[3] = {-P.D * sa * sp - P.D * ca * cp, P.D * sa * cp - P.D * ca * sp, w};
     // entry / exit of the volume box (slab method)
     double tin = -1e300, tout = 1e300;
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const double hi = P.lo[ax] + P.n[ax] * P.vs[ax];
         if (d[ax] == 0.0) {
@@ -69,41 +70,80 @@ __global__ void __launch_bounds__(256) k_project(ProjArgs P, const float *__rest
         return;
     }
     const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    // traversal in voxel units relative to the entry point, parameter s in [0, T] along d
-    float u[3], inv[3], tb[3];
-    int ix[3], step[3];
+    // traversal in voxel units relative to the entry point, parameter s in [0, T] along d; one
+    // scalar set per axis (no per-axis arrays: indexing them by the crossing axis would put them
+    // in local memory)
     const float T = (float)(tout - tin);
-    for (int ax = 0; ax < 3; ++ax) {
-        u[ax] = (float)((a[ax] + tin * d[ax] - P.lo[ax]) / P.vs[ax]);
+    float ux, uy, uz, ivx, ivy, ivz, tx, ty, tz;
+    int ixx, iyy, izz, sx, sy, sz;
+    auto axis_setup = [&](int ax, float *uu, float *iv, float *tb, int *ii, int *st) {
+        *uu = (float)((a[ax] + tin * d[ax] - P.lo[ax]) / P.vs[ax]);
         const float du = (float)(d[ax] / P.vs[ax]);
-        ix[ax] = min(max((int)floorf(u[ax]), 0), P.n[ax] - 1);
+        *ii = min(max((int)floorf(*uu), 0), P.n[ax] - 1);
         if (du > 0.0f) {
-            step[ax] = 1;
-            inv[ax] = 1.0f / du;
-            tb[ax] = ((float)(ix[ax] + 1) - u[ax]) * inv[ax];
+            *st = 1;
+            *iv = 1.0f / du;
+            *tb = ((float)(*ii + 1) - *uu) * *iv;
         } else if (du < 0.0f) {
-            step[ax] = -1;
-            inv[ax] = 1.0f / du;
-            tb[ax] = ((float)ix[ax] - u[ax]) * inv[ax];
+            *st = -1;
+            *iv = 1.0f / du;
+            *tb = ((float)*ii - *uu) * *iv;
         } else {
-            step[ax] = 0;
-            inv[ax] = 0.0f;
-            tb[ax] = INFINITY;
+            *st = 0;
+            *iv = 0.0f;
+            *tb = INFINITY;
         }
-    }
+    };
+    axis_setup(0, &ux, &ivx, &tx, &ixx, &sx);
+    axis_setup(1, &uy, &ivy, &ty, &iyy, &sy);
+    axis_setup(2, &uz, &ivz, &tz, &izz, &sz);
     const int nx = P.n[0], nxy = P.n[0] * P.n[1];
     float acc = 0.0f, s = 0.0f;
     const int max_steps = P.n[0] + P.n[1] + P.n[2] + 3;
-    for (int it = 0; it < max_steps; ++it) {
-        const int m = (tb[0] <= tb[1]) ? (tb[0] <= tb[2] ? 0 : 2) : (tb[1] <= tb[2] ? 1 : 2);
-        const float sn = fminf(tb[m], T);
-        acc = fmaf(sn - s, __ldg(vol + ix[2] * nxy + ix[1] * nx + ix[0]), acc);
-        if (sn >= T) break;
-        s = sn;
-        ix[m] += step[m];
-        if (ix[m] < 0 || ix[m] >= P.n[m]) break;
-        // the next face of this axis, from its plane index
-        tb[m] = ((float)(step[m] > 0 ? ix[m] + 1 : ix[m]) - u[m]) * inv[m];
+    // The next voxel follows from the face crossings alone, not from the loaded values: walk
+    // UNROLL segments (ALU only), then load their voxels together so the loads overlap.
+    constexpr int UNROLL = 4;
+    bool done = false;
+    int idx = izz * nxy + iyy * nx + ixx;
+    for (int it = 0; it < max_steps && !done; it += UNROLL) {
+        float seg[UNROLL];
+        int vi[UNROLL];
+#pragma unroll
+        for (int q = 0; q < UNROLL; ++q) {
+            vi[q] = idx;  // a finished ray repeats a valid voxel with zero length
+            seg[q] = 0.0f;
+            if (!done) {
+                const bool mx = tx <= ty && tx <= tz, my = !mx && ty <= tz, mz = !mx && !my;
+                const float sn = fminf(fminf(fminf(tx, ty), tz), T);
+                seg[q] = sn - s;
+                s = sn;
+                if (sn >= T) {
+                    done = true;
+                } else {
+                    // cross the nearest face; its axis's next face from the plane index
+                    if (mx) {
+                        ixx += sx;
+                        tx = ((float)(sx > 0 ? ixx + 1 : ixx) - ux) * ivx;
+                    } else if (my) {
+                        iyy += sy;
+                        ty = ((float)(sy > 0 ? iyy + 1 : iyy) - uy) * ivy;
+                    } else {
+                        izz += sz;
+                        tz = ((float)(sz > 0 ? izz + 1 : izz) - uz) * ivz;
+                    }
+                    (void)mz;
+                    if (ixx < 0 || ixx >= P.n[0] || iyy < 0 || iyy >= P.n[1] || izz < 0 || izz >= P.n[2])
+                        done = true;
+                    else
+                        idx = izz * nxy + iyy * nx + ixx;
+                }
+            }
+        }
+        float v[UNROLL];
+#pragma unroll
+        for (int q = 0; q < UNROLL; ++q) v[q] = __ldg(vol + vi[q]);
+#pragma unroll
+        for (int q = 0; q < UNROLL; ++q) acc = fmaf(seg[q], v[q], acc);
     }
     sino[t] = (float)((double)acc * len);
 }
