@@ -17,7 +17,8 @@
 // the seed with counter (sample index, draw, stream), two 53-bit uniforms per
 // call; Poisson variates by transformed rejection (PTRS, Hormann 1993) for
 // means >= 10 and multiplication of uniforms below; normal variates by
-// Box-Muller.  Everything that decides a draw is FP64.
+// Box-Muller.  Everything that decides a draw is FP64; the normal variate and
+// the final log, which only perturb the float output, are FP32.
 #include <cstdint>
 #include <cstring>
 
@@ -232,9 +233,9 @@ __device__ int64_t poisson_draw(double lam, uint64_t seed, int64_t i)
         }
         return k;
     }
-    const double slam = sqrt(lam), loglam = log(lam);
+    const double slam = sqrt(lam);
     const double b = 0.931 + 2.53 * slam, a = -0.059 + 0.02483 * b;
-    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4), vr = 0.9277 - 3.6224 / (b - 2.0);
+    const double vr = 0.9277 - 3.6224 / (b - 2.0);
     for (uint32_t draw = 0; draw < (1u << 20); ++draw) {  // acceptance is > 85% per draw
         double u, v;
         uniforms(seed, i, draw, 0u, &u, &v);
@@ -243,6 +244,8 @@ __device__ int64_t poisson_draw(double lam, uint64_t seed, int64_t i)
         const double k = floor((2.0 * a / us + b) * u + lam + 0.43);
         if (us >= 0.07 && v <= vr) return (int64_t)k;
         if (k < 0.0 || (us < 0.013 && v > us)) continue;
+        // the rare full test (its constants computed here, not on the common path)
+        const double loglam = log(lam), inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
         if (log(v) + log(inv_alpha) - log(a / (us * us) + b) <= -lam + k * loglam - log_factorial(k))
             return (int64_t)k;
     }
@@ -267,11 +270,13 @@ __global__ void k_noise(const float *__restrict__ g_up, float *__restrict__ g_in
         const double lam = M > 0.0 ? I0 * exp(-(double)g_up[i] / M) : I0;
         const int64_t k = poisson_draw(lam, seed, i);
         if (counts) counts[i] = k;
+        // the normal variate and the log only perturb a float output: FP32 (their rounding moves
+        // g_in by ~1e-7 M; the integer draw above is decided in FP64)
         double u0, u1;
         uniforms(seed, i, 0u, 1u, &u0, &u1);
-        double q = (double)k + mean + sd * (sqrt(-2.0 * log(u0)) * cos(2.0 * kPi * u1));
-        if (q < 1.0) q = 1.0;
-        g_in[i] = (float)(log(I0 / q) * M);
+        const float z = sqrtf(-2.0f * logf((float)u0)) * cospif(2.0f * (float)u1);
+        const float q = fmaxf((float)k + (float)mean + (float)sd * z, 1.0f);
+        g_in[i] = (float)M * logf((float)I0 / q);
     }
 }
 
