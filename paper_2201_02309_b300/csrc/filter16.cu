@@ -70,36 +70,35 @@ __global__ void k_deriv_rebin16(const float *__restrict__ sino, uint16_t *__rest
 }
 
 // Steps 5-6 into the row-pair layout: word (pair-row pr, column c) holds
-// (g^F[pr-1][c], g^F[pr][c]) in its low / high 16 bits, zero outside the detector.
+// (g^F[pr-1][c], g^F[pr][c]) in its low / high 16 bits, zero outside the
+// detector.  A thread walks one column of one view down the rows, so each
+// row's value is computed once and lands in two words.
 template <bool FP16>
 __global__ void k_unrebin_cos16(const float *__restrict__ g4, uint32_t *__restrict__ gFp,
                                 const int32_t *__restrict__ psi_idx, const float *__restrict__ psi_frac,
                                 const float *__restrict__ cosa, int64_t nv, int n_rows, int n_cols, int n_psi,
                                 int gcols, int ld4)
 {
-    const int prows = n_rows + 1;
-    const int64_t per = (int64_t)prows * gcols;
-    const int64_t total = nv * per;
+    const int64_t total = nv * gcols;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / per;
-        const int rr = (int)(t % per);
-        const int pr = rr / gcols, c = rr % gcols;
-        float val[2] = {0.0f, 0.0f};
-        if (c < n_cols) {
-            const float *col = g4 + v * n_psi * ld4 + c;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = pr - 1 + h;
-                if (r < 0 || r >= n_rows) continue;
+        const int64_t v = t / gcols;
+        const int c = (int)(t % gcols);
+        uint32_t *out = gFp + v * (int64_t)(n_rows + 1) * gcols + c;
+        uint32_t prev = 0;  // 16-bit value of row pr - 1
+        const float *col = g4 + v * n_psi * ld4 + c;
+        for (int r = 0; r <= n_rows; ++r) {
+            uint32_t cur = 0;
+            if (r < n_rows && c < n_cols) {
                 const int rc = r * n_cols + c;
                 const int l = psi_idx[rc];
                 const float f = psi_frac[rc];
                 const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
                 const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
-                val[h] = cosa[c] * ((1.0f - f) * lo + f * hi);
+                cur = to16<FP16>(cosa[c] * ((1.0f - f) * lo + f * hi));
             }
+            out[(int64_t)r * gcols] = prev | (cur << 16);
+            prev = cur;
         }
-        gFp[t] = (uint32_t)to16<FP16>(val[0]) | ((uint32_t)to16<FP16>(val[1]) << 16);
     }
 }
 
@@ -132,7 +131,7 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
         set_error("the 16-bit Hilbert step needs the tensor-core path (TMA encoder or alignment unavailable)");
         return KATS_EINVAL;
     }
-    const int64_t total = nv * (nr + 1) * p.gf_cols;
+    const int64_t total = nv * p.gf_cols;
     auto ku = fp16 ? k_unrebin_cos16<true> : k_unrebin_cos16<false>;
     ku<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
         g4, gFp, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols, (int)p.tc_n);
