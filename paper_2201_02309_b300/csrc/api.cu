@@ -118,8 +118,15 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     const size_t fws_bytes = recon_ws_for(p, precision) - gfb;
     const int64_t nf = p.n_fviews, nz = p.g.nz, nxy = p.g.nx * p.g.ny;
     const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, nf / 256));
-    const int slab = (int)std::max<int64_t>(16, ((nz + 5) / 6 + 15) / 16 * 16);  // about 6 slabs of whole z tiles
-    const int n_slabs = (int)((nz + slab - 1) / slab);
+    // slabs of whole 16-slice z tiles: a small first slab starts backprojecting after few chunks, a
+    // small last slab leaves little to copy back at the end, the middle ones are 64 slices
+    std::vector<int> slab_lo{0};
+    while (slab_lo.back() < nz) {
+        const int64_t s0 = slab_lo.back(), left = nz - s0;
+        const int64_t n = s0 == 0 ? 16 : (left <= 80 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 64);
+        slab_lo.push_back((int)std::min<int64_t>(nz, s0 + std::max<int64_t>(n, 1)));
+    }
+    const int n_slabs = (int)slab_lo.size() - 1;
     auto chunk_lo = [&](int i) { return nf * i / n_chunks; };
 
     cudaStream_t cs = nullptr;
@@ -143,7 +150,7 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     }
     int filtered = 0;  // chunks already filtered on st
     for (int j = 0; !rc && e == cudaSuccess && j < n_slabs; ++j) {
-        const int s0 = j * slab, n = (int)std::min<int64_t>(slab, nz - s0);
+        const int s0 = slab_lo[(size_t)j], n = slab_lo[(size_t)j + 1] - s0;
         int64_t lo, hi;
         slab_views(p, s0, s0 + n, &lo, &hi);
         // filter every chunk up to the one holding the slab's last view
