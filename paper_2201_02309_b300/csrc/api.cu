@@ -99,8 +99,8 @@ static void slab_views(const Plan &p, int64_t s0, int64_t s1, int64_t *lo, int64
 
 // One item from host buffers, stream-ordered and asynchronous: copy the view
 // window the volume needs, steps 1-7, copy the volume back.  ws holds
-// host_item_bytes(p, precision) bytes.  The copies overlap the kernels: the
-// window arrives in chunks on a second stream; a slab of slices is
+// host_item_bytes(p, precision) bytes.  For windows of 128 MiB and more the
+// copies overlap the kernels: the window arrives in chunks on a second stream; a slab of slices is
 // backprojected as soon as the chunks holding its views are filtered (the PI
 // windows rise with z), while later chunks are still arriving; each slab of
 // the volume is copied back while later slabs are backprojected.  Work issued
@@ -117,6 +117,14 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     char *fws = rws + gfb;
     const size_t fws_bytes = recon_ws_for(p, precision) - gfb;
     const int64_t nf = p.n_fviews, nz = p.g.nz, nxy = p.g.nx * p.g.ny;
+    if (win < ((size_t)128 << 20)) {
+        // small items: copies are short, a second stream and events would cost more than they hide
+        KATS_CUDA(cudaMemcpyAsync(d_win, host_sino + p.first_view * view, win, cudaMemcpyHostToDevice, st));
+        int rc = recon_item(p, precision, d_win, d_vol, rws, recon_ws_for(p, precision), st);
+        if (rc) return rc;
+        KATS_CUDA(cudaMemcpyAsync(host_vol, d_vol, sizeof(float) * vol_item(p), cudaMemcpyDeviceToHost, st));
+        return KATS_OK;
+    }
     const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, nf / 256));
     // slabs of whole 16-slice z tiles: a small first slab starts backprojecting after few chunks, a
     // small last slab leaves little to copy back at the end, the middle ones are 64 slices
