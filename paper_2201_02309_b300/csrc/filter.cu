@@ -26,42 +26,57 @@ size_t filter_workspace_bytes(const Plan &p)
 }
 
 // ---------------------------------------------------------------- steps 1-3
-// grid (ceil(Kp / 32), n_fviews); block 256; dynamic smem n_rows * 32 floats.
-__global__ void k_deriv_rebin(const float *__restrict__ sino, float *__restrict__ g3, const int32_t *__restrict__ kap_idx,
-                              const float *__restrict__ kap_frac, const float *__restrict__ lw, int nv, int n_rows, int n_cols, int n_psi, int Kp, float a_lam, float a_alp)
+// grid (ceil(Kp / 32), ceil(n_fviews / views_per_block)); block 256 (8 warps); dynamic smem
+// n_rows * 32 floats (g2 of one view), plus with CACHED n_psi * 32 (int, float) kappa-table
+// entries.  A block handles 32 columns of consecutive views; CACHED reads its columns' table
+// entries once instead of once per view.
+template <bool CACHED>
+__global__ void __launch_bounds__(256) k_deriv_rebin(const float *__restrict__ sino, float *__restrict__ g3,
+                                                     const int32_t *__restrict__ kap_idx,
+                                                     const float *__restrict__ kap_frac, const float *__restrict__ lw,
+                                                     int nv, int n_rows, int n_cols, int n_psi, int Kp, float a_lam,
+                                                     float a_alp, int views_per_block)
 {
     extern __shared__ float s_g2[];  // [n_rows][32]
+    int *s_ki = reinterpret_cast<int *>(s_g2 + n_rows * 32);  // [n_psi][32]
+    float *s_kf = reinterpret_cast<float *>(s_ki + n_psi * 32);
     const int nc1 = n_cols - 1;
     const int c0 = blockIdx.x * 32;
-    const int cc = threadIdx.x & 31;
+    const int cc = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = c0 + cc;
-    for (int v = blockIdx.y; v < nv; v += gridDim.y) {
-    const float *p0 = sino + (int64_t)v * n_rows * n_cols;  // sino points at sinogram view first_view
-    const float *p1 = p0 + (int64_t)n_rows * n_cols;
-    __syncthreads();  // s_g2 of the previous view fully consumed
-    for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) {
-        float val = 0.0f;
-        if (c < nc1) {
-            const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
-            const float d = p1[r * n_cols + c], e = p1[r * n_cols + c + 1];
-            // (dg/dlambda + dg/dalpha) at the cell centre, times D / sqrt(D^2 + w^2)
-            val = lw[r] * (a_lam * ((d - a) + (e - b)) + a_alp * ((b - a) + (e - d)));
+    if (CACHED)
+        for (int l = warp; l < n_psi; l += 8) {
+            s_ki[l * 32 + cc] = c < nc1 ? kap_idx[l * nc1 + c] : -2;  // -2: no tap, both rows out of range
+            s_kf[l * 32 + cc] = c < nc1 ? kap_frac[l * nc1 + c] : 0.0f;
         }
-        s_g2[r * 32 + cc] = val;
-    }
-    __syncthreads();
-    float *out = g3 + (int64_t)v * n_psi * Kp;
-    for (int l = threadIdx.x >> 5; l < n_psi; l += blockDim.x >> 5) {
-        float val = 0.0f;
-        if (c < nc1) {
-            const int r = kap_idx[l * nc1 + c];
-            const float f = kap_frac[l * nc1 + c];
-            const float lo = (r >= 0 && r < n_rows) ? s_g2[r * 32 + cc] : 0.0f;
-            const float hi = (r + 1 >= 0 && r + 1 < n_rows) ? s_g2[(r + 1) * 32 + cc] : 0.0f;
-            val = (1.0f - f) * lo + f * hi;
+    const int vb = blockIdx.y * views_per_block, ve = min(vb + views_per_block, nv);
+    for (int v = vb; v < ve; ++v) {
+        const float *p0 = sino + (int64_t)v * n_rows * n_cols;  // sino points at sinogram view first_view
+        const float *p1 = p0 + (int64_t)n_rows * n_cols;
+        __syncthreads();  // s_g2 of the previous view consumed (first pass: tables written)
+#pragma unroll 4
+        for (int r = warp; r < n_rows; r += 8) {
+            float val = 0.0f;
+            if (c < nc1) {
+                const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
+                const float d = p1[r * n_cols + c], e = p1[r * n_cols + c + 1];
+                // (dg/dlambda + dg/dalpha) at the cell centre, times D / sqrt(D^2 + w^2)
+                val = lw[r] * (a_lam * ((d - a) + (e - b)) + a_alp * ((b - a) + (e - d)));
+            }
+            s_g2[r * 32 + cc] = val;
         }
-        if (c < Kp) out[(int64_t)l * Kp + c] = val;
-    }
+        __syncthreads();
+        if (c < Kp) {
+            float *out = g3 + (int64_t)v * n_psi * Kp + c;
+#pragma unroll 4
+            for (int l = warp; l < n_psi; l += 8) {
+                const int r = CACHED ? s_ki[l * 32 + cc] : (c < nc1 ? kap_idx[l * nc1 + c] : -2);
+                const float f = CACHED ? s_kf[l * 32 + cc] : (c < nc1 ? kap_frac[l * nc1 + c] : 0.0f);
+                const float lo = (r >= 0 && r < n_rows) ? s_g2[r * 32 + cc] : 0.0f;
+                const float hi = (r + 1 >= 0 && r + 1 < n_rows) ? s_g2[(r + 1) * 32 + cc] : 0.0f;
+                out[(int64_t)l * Kp] = (1.0f - f) * lo + f * hi;
+            }
+        }
     }
 }
 
@@ -136,27 +151,40 @@ __global__ void __launch_bounds__(256) k_toeplitz_gemm(const float *__restrict__
 
 // ---------------------------------------------------------------- steps 5-6
 // gF rows have pitch gcols >= n_cols; the pad columns are written as zeros.
-__global__ void k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ gF, const int32_t *__restrict__ psi_idx,
-                              const float *__restrict__ psi_frac, const float *__restrict__ cosa, int64_t nv,
-                              int n_rows, int n_cols, int n_psi, int gcols, int ld4)
+// grid (ceil(gcols / 32), ceil(n_fviews / views_per_block)); block 256 (8 warps); dynamic smem
+// n_rows * 32 (int, float) psi-table entries with CACHED, read once per block for its 32 columns
+// instead of once per view.
+template <bool CACHED>
+__global__ void __launch_bounds__(256) k_unrebin_cos(const float *__restrict__ g4, float *__restrict__ gF,
+                                                     const int32_t *__restrict__ psi_idx,
+                                                     const float *__restrict__ psi_frac,
+                                                     const float *__restrict__ cosa, int64_t nv, int n_rows,
+                                                     int n_cols, int n_psi, int gcols, int ld4, int views_per_block)
 {
-    const int64_t per = (int64_t)n_rows * gcols;
-    const int64_t total = nv * per;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / per;
-        const int rr = (int)(t % per);
-        const int r = rr / gcols, c = rr % gcols;
-        if (c >= n_cols) {
-            gF[t] = 0.0f;
-            continue;
+    extern __shared__ int s_li[];  // [n_rows][32]
+    float *s_lf = reinterpret_cast<float *>(s_li + n_rows * 32);
+    const int cc = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cc;
+    if (CACHED)
+        for (int r = warp; r < n_rows; r += 8) {
+            s_li[r * 32 + cc] = c < n_cols ? psi_idx[r * n_cols + c] : -2;  // -2: no tap, both lines out of range
+            s_lf[r * 32 + cc] = c < n_cols ? psi_frac[r * n_cols + c] : 0.0f;
         }
-        const int rc = r * n_cols + c;
-        const int l = psi_idx[rc];
-        const float f = psi_frac[rc];
+    const float w = c < n_cols ? cosa[c] : 0.0f;  // pad columns get 0
+    __syncthreads();
+    if (c >= gcols) return;
+    const int64_t vb = (int64_t)blockIdx.y * views_per_block, ve = min(vb + views_per_block, nv);
+    for (int64_t v = vb; v < ve; ++v) {
         const float *col = g4 + v * n_psi * ld4 + c;
-        const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
-        const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
-        gF[t] = cosa[c] * ((1.0f - f) * lo + f * hi);
+        float *out = gF + v * (int64_t)n_rows * gcols + c;
+#pragma unroll 4
+        for (int r = warp; r < n_rows; r += 8) {
+            const int l = CACHED ? s_li[r * 32 + cc] : (c < n_cols ? psi_idx[r * n_cols + c] : -2);
+            const float f = CACHED ? s_lf[r * 32 + cc] : (c < n_cols ? psi_frac[r * n_cols + c] : 0.0f);
+            const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
+            const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
+            out[(int64_t)r * gcols] = w * ((1.0f - f) * lo + f * hi);
+        }
     }
 }
 
@@ -172,11 +200,17 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
     float *g3 = (float *)ws;
     float *g4 = g3 + p.n_fviews * np * Kp;  // workspace laid out for every view; a chunk uses the front
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
-    const size_t smem = sizeof(float) * 32 * (size_t)nr;
-    if (smem > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_deriv_rebin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 g1((unsigned)ceil_div(Kp, 32), (unsigned)std::min<int64_t>(nv, 65535));
-    k_deriv_rebin<<<g1, 256, smem, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc,
-                                         (int)np, (int)Kp, a_lam, a_alp);
+    // Table entries stay in shared memory while that leaves room for several blocks per SM.
+    constexpr size_t kCacheMax = 64 * 1024;
+    const size_t smem1 = sizeof(float) * 32 * (size_t)nr, tab1 = 8 * 32 * (size_t)np;
+    const bool cache1 = tab1 <= kCacheMax;
+    const int vpb = (int)std::max<int64_t>(8, ceil_div(nv, 65535));  // views per block
+    dim3 g1((unsigned)ceil_div(Kp, 32), (unsigned)ceil_div(nv, vpb));
+    auto kd = cache1 ? k_deriv_rebin<true> : k_deriv_rebin<false>;
+    const size_t sm1 = smem1 + (cache1 ? tab1 : 0);
+    if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    kd<<<g1, 256, sm1, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp,
+                             a_lam, a_alp, vpb);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
     const int ld4 = (int)p.tc_n;
@@ -192,9 +226,14 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
         k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, ld4, (int)nc, 0);
         KATS_CUDA(cudaGetLastError());
     }
-    const int64_t total = nv * nr * p.gf_cols;
-    k_unrebin_cos<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
-        g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols, ld4);
+    dim3 g3d((unsigned)ceil_div(p.gf_cols, 32), (unsigned)ceil_div(nv, vpb));
+    const size_t tab3 = 8 * 32 * (size_t)nr;
+    const bool cache3 = tab3 <= kCacheMax;
+    auto ku = cache3 ? k_unrebin_cos<true> : k_unrebin_cos<false>;
+    if (cache3 && tab3 > 48 * 1024)
+        KATS_CUDA(cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab3));
+    ku<<<g3d, 256, cache3 ? tab3 : 0, st>>>(g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np,
+                                         (int)p.gf_cols, ld4, vpb);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }

@@ -29,22 +29,34 @@ size_t filter16_workspace_bytes(const Plan &p)
 }
 
 // Steps 1-3 as k_deriv_rebin, output g3 * d_alpha in 16 bits, rows of tc_k16 (zero tail).
-template <bool FP16>
-__global__ void k_deriv_rebin16(const float *__restrict__ sino, uint16_t *__restrict__ g3,
-                                const int32_t *__restrict__ kap_idx, const float *__restrict__ kap_frac,
-                                const float *__restrict__ lw, int nv, int n_rows, int n_cols, int n_psi, int Kp,
-                                float a_lam, float a_alp, float scale)
+// grid (ceil(tc_k16 / 32), ceil(n_fviews / views_per_block)); block 256; dynamic smem n_rows * 32
+// floats, plus with CACHED the block's n_psi * 32 (int, float) kappa-table entries.
+template <bool FP16, bool CACHED>
+__global__ void __launch_bounds__(256) k_deriv_rebin16(const float *__restrict__ sino, uint16_t *__restrict__ g3,
+                                                       const int32_t *__restrict__ kap_idx,
+                                                       const float *__restrict__ kap_frac,
+                                                       const float *__restrict__ lw, int nv, int n_rows, int n_cols,
+                                                       int n_psi, int Kp, float a_lam, float a_alp, float scale,
+                                                       int views_per_block)
 {
     extern __shared__ float s_g2[];  // [n_rows][32]
+    int *s_ki = reinterpret_cast<int *>(s_g2 + n_rows * 32);  // [n_psi][32]
+    float *s_kf = reinterpret_cast<float *>(s_ki + n_psi * 32);
     const int nc1 = n_cols - 1;
-    const int c0 = blockIdx.x * 32;
-    const int cc = threadIdx.x & 31;
-    const int c = c0 + cc;
-    for (int v = blockIdx.y; v < nv; v += gridDim.y) {
+    const int cc = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cc;
+    if (CACHED)
+        for (int l = warp; l < n_psi; l += 8) {
+            s_ki[l * 32 + cc] = c < nc1 ? kap_idx[l * nc1 + c] : -2;  // -2: no tap
+            s_kf[l * 32 + cc] = c < nc1 ? kap_frac[l * nc1 + c] : 0.0f;
+        }
+    const int vb = blockIdx.y * views_per_block, ve = min(vb + views_per_block, nv);
+    for (int v = vb; v < ve; ++v) {
         const float *p0 = sino + (int64_t)v * n_rows * n_cols;
         const float *p1 = p0 + (int64_t)n_rows * n_cols;
         __syncthreads();
-        for (int r = threadIdx.x >> 5; r < n_rows; r += blockDim.x >> 5) {
+#pragma unroll 4
+        for (int r = warp; r < n_rows; r += 8) {
             float val = 0.0f;
             if (c < nc1) {
                 const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
@@ -54,17 +66,16 @@ __global__ void k_deriv_rebin16(const float *__restrict__ sino, uint16_t *__rest
             s_g2[r * 32 + cc] = val;
         }
         __syncthreads();
-        uint16_t *out = g3 + (int64_t)v * n_psi * Kp;
-        for (int l = threadIdx.x >> 5; l < n_psi; l += blockDim.x >> 5) {
-            float val = 0.0f;
-            if (c < nc1) {
-                const int r = kap_idx[l * nc1 + c];
-                const float f = kap_frac[l * nc1 + c];
+        if (c < Kp) {
+            uint16_t *out = g3 + (int64_t)v * n_psi * Kp + c;
+#pragma unroll 4
+            for (int l = warp; l < n_psi; l += 8) {
+                const int r = CACHED ? s_ki[l * 32 + cc] : (c < nc1 ? kap_idx[l * nc1 + c] : -2);
+                const float f = CACHED ? s_kf[l * 32 + cc] : (c < nc1 ? kap_frac[l * nc1 + c] : 0.0f);
                 const float lo = (r >= 0 && r < n_rows) ? s_g2[r * 32 + cc] : 0.0f;
                 const float hi = (r + 1 >= 0 && r + 1 < n_rows) ? s_g2[(r + 1) * 32 + cc] : 0.0f;
-                val = (1.0f - f) * lo + f * hi;
+                out[(int64_t)l * Kp] = to16<FP16>(((1.0f - f) * lo + f * hi) * scale);
             }
-            if (c < Kp) out[(int64_t)l * Kp + c] = to16<FP16>(val * scale);
         }
     }
 }
@@ -72,33 +83,45 @@ __global__ void k_deriv_rebin16(const float *__restrict__ sino, uint16_t *__rest
 // Steps 5-6 into the row-pair layout: word (pair-row pr, column c) holds
 // (g^F[pr-1][c], g^F[pr][c]) in its low / high 16 bits, zero outside the
 // detector.  A thread walks one column of one view down the rows, so each
-// row's value is computed once and lands in two words.
-template <bool FP16>
-__global__ void k_unrebin_cos16(const float *__restrict__ g4, uint32_t *__restrict__ gFp,
-                                const int32_t *__restrict__ psi_idx, const float *__restrict__ psi_frac,
-                                const float *__restrict__ cosa, int64_t nv, int n_rows, int n_cols, int n_psi,
-                                int gcols, int ld4)
+// row's value is computed once and lands in two words.  grid (ceil(gcols / 32),
+// ceil(n_fviews / (8 * views_per_warp))); block 256: warp w of a block takes views
+// w, w + 8, ... of the block's range for the block's 32 columns; with CACHED the
+// columns' psi-table entries (n_rows * 32 (int, float)) sit in shared memory.
+template <bool FP16, bool CACHED>
+__global__ void __launch_bounds__(256) k_unrebin_cos16(const float *__restrict__ g4, uint32_t *__restrict__ gFp,
+                                                       const int32_t *__restrict__ psi_idx,
+                                                       const float *__restrict__ psi_frac,
+                                                       const float *__restrict__ cosa, int64_t nv, int n_rows,
+                                                       int n_cols, int n_psi, int gcols, int ld4, int views_per_warp)
 {
-    const int64_t total = nv * gcols;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / gcols;
-        const int c = (int)(t % gcols);
+    extern __shared__ int s_li[];  // [n_rows][32]
+    float *s_lf = reinterpret_cast<float *>(s_li + n_rows * 32);
+    const int cc = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cc;
+    if (CACHED)
+        for (int r = warp; r < n_rows; r += 8) {
+            s_li[r * 32 + cc] = c < n_cols ? psi_idx[r * n_cols + c] : -2;  // -2: no tap
+            s_lf[r * 32 + cc] = c < n_cols ? psi_frac[r * n_cols + c] : 0.0f;
+        }
+    const float w = c < n_cols ? cosa[c] : 0.0f;
+    __syncthreads();
+    if (c >= gcols) return;
+    const int64_t vb = (int64_t)blockIdx.y * 8 * views_per_warp, ve = min(vb + 8 * views_per_warp, nv);
+    for (int64_t v = vb + warp; v < ve; v += 8) {
         uint32_t *out = gFp + v * (int64_t)(n_rows + 1) * gcols + c;
         uint32_t prev = 0;  // 16-bit value of row pr - 1
         const float *col = g4 + v * n_psi * ld4 + c;
-        for (int r = 0; r <= n_rows; ++r) {
-            uint32_t cur = 0;
-            if (r < n_rows && c < n_cols) {
-                const int rc = r * n_cols + c;
-                const int l = psi_idx[rc];
-                const float f = psi_frac[rc];
-                const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
-                const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
-                cur = to16<FP16>(cosa[c] * ((1.0f - f) * lo + f * hi));
-            }
+#pragma unroll 4
+        for (int r = 0; r < n_rows; ++r) {
+            const int l = CACHED ? s_li[r * 32 + cc] : (c < n_cols ? psi_idx[r * n_cols + c] : -2);
+            const float f = CACHED ? s_lf[r * 32 + cc] : (c < n_cols ? psi_frac[r * n_cols + c] : 0.0f);
+            const float lo = (l >= 0 && l < n_psi) ? col[(int64_t)l * ld4] : 0.0f;
+            const float hi = (l + 1 >= 0 && l + 1 < n_psi) ? col[(int64_t)(l + 1) * ld4] : 0.0f;
+            const uint32_t cur = to16<FP16>(w * ((1.0f - f) * lo + f * hi));  // pad columns: w = 0, no taps
             out[(int64_t)r * gcols] = prev | (cur << 16);
             prev = cur;
         }
+        out[(int64_t)n_rows * gcols] = prev;
     }
 }
 
@@ -117,12 +140,17 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
     float *g4 = (float *)((char *)ws + ((size_t)(p.n_fviews * np) * (size_t)p.tc_k16 * 2 + 255) / 256 * 256);
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     const float scale = (float)p.g.d_alpha;
-    const size_t smem = sizeof(float) * 32 * (size_t)nr;
-    auto kd = fp16 ? k_deriv_rebin16<true> : k_deriv_rebin16<false>;
-    if (smem > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 g1((unsigned)ceil_div(p.tc_k16, 32), (unsigned)std::min<int64_t>(nv, 65535));
-    kd<<<g1, 256, smem, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np,
-                              (int)p.tc_k16, a_lam, a_alp, scale);
+    constexpr size_t kCacheMax = 64 * 1024;  // table entries in shared memory up to this size
+    const size_t smem1 = sizeof(float) * 32 * (size_t)nr, tab1 = 8 * 32 * (size_t)np;
+    const bool cache1 = tab1 <= kCacheMax;
+    auto kd = fp16 ? (cache1 ? k_deriv_rebin16<true, true> : k_deriv_rebin16<true, false>)
+                   : (cache1 ? k_deriv_rebin16<false, true> : k_deriv_rebin16<false, false>);
+    const size_t sm1 = smem1 + (cache1 ? tab1 : 0);
+    if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    const int vpb = (int)std::max<int64_t>(8, ceil_div(nv, 65535));  // views per block
+    dim3 g1((unsigned)ceil_div(p.tc_k16, 32), (unsigned)ceil_div(nv, vpb));
+    kd<<<g1, 256, sm1, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np,
+                             (int)p.tc_k16, a_lam, a_alp, scale, vpb);
     KATS_CUDA(cudaGetLastError());
     bool tc = false;
     int rc = launch_hilbert_tc16(p, prec, g3, g4, M, (int)p.tc_n, st, &tc);
@@ -131,10 +159,16 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
         set_error("the 16-bit Hilbert step needs the tensor-core path (TMA encoder or alignment unavailable)");
         return KATS_EINVAL;
     }
-    const int64_t total = nv * p.gf_cols;
-    auto ku = fp16 ? k_unrebin_cos16<true> : k_unrebin_cos16<false>;
-    ku<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
-        g4, gFp, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np, (int)p.gf_cols, (int)p.tc_n);
+    const size_t tab3 = 8 * 32 * (size_t)nr;
+    const bool cache3 = tab3 <= kCacheMax;
+    auto ku = fp16 ? (cache3 ? k_unrebin_cos16<true, true> : k_unrebin_cos16<true, false>)
+                   : (cache3 ? k_unrebin_cos16<false, true> : k_unrebin_cos16<false, false>);
+    if (cache3 && tab3 > 48 * 1024)
+        KATS_CUDA(cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab3));
+    const int vpw = (int)std::max<int64_t>(2, ceil_div(nv, 8 * 65535));  // views per warp
+    dim3 g3d((unsigned)ceil_div(p.gf_cols, 32), (unsigned)ceil_div(nv, 8 * vpw));
+    ku<<<g3d, 256, cache3 ? tab3 : 0, st>>>(g4, gFp, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np,
+                                         (int)p.gf_cols, (int)p.tc_n, vpw);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
