@@ -112,6 +112,10 @@ typedef struct kats_plan_info {
     int64_t gf_cols;          /* row pitch of filtered data: n_cols rounded up to 4    */
     int64_t workspace_bytes;  /* per concurrent call, FP32 storage                     */
     int64_t plan_bytes;       /* device bytes held by the plan                         */
+    int64_t pi_monotone;      /* 1: every voxel column's PI-window start and end (with
+                               * end weights) are nondecreasing in z, the property the
+                               * backprojection's ramp handling uses; 0: it takes the
+                               * general per-slice weights                             */
 } kats_plan_info;
 
 /*

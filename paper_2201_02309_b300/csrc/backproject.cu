@@ -184,6 +184,7 @@ struct BP2Args {
     int slot_floats;  // floats per staged view, multiple of 32 (128-byte slots)
     int *status;
     float out_scale;  // dl / 2pi, divided by d_alpha for the scaled 16-bit storage
+    int mono;         // window starts and ends nondecreasing in the slice (plan check)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -320,6 +321,36 @@ __device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float 
         } else {
             bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), acc2[pr]);
         }
+    }
+}
+
+// One view in a ramp of the thread's slice windows, the windows nondecreasing in
+// the slice.  IN: no slice has ended and some have not started, so the slices
+// the view reaches are a prefix with weights sat(k - lo); otherwise every slice
+// has started, the open ones are a suffix with weights sat(hi - k).  The pair
+// loop stops at the first pair outside; in a boundary pair the closed slice reads
+// its partner's rows (its weight is 0), so the rows stay inside the staged window
+// without clamping.  The weights and taps equal the general weighted path's.
+template <int PITCH, int MODE, bool IN, bool CLAMP>
+__device__ __forceinline__ void bp_view_ramp(const float *smem, uint32_t colx, float fc, float ur0, float dur,
+                                             float rmax, float inv_v, float kf, const float *lo, const float *hi,
+                                             float2 *acc2)
+{
+    const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
+    const float2 iv2 = make_float2(inv_v, inv_v);
+    const __half2 fch = __float2half2_rn(fc);
+#pragma unroll
+    for (int i = 0; i < B2_T / 2; ++i) {
+        const int pr = IN ? i : B2_T / 2 - 1 - i;
+        if (IN ? !(kf > lo[2 * pr]) : !(kf < hi[2 * pr + 1])) break;
+        float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
+        const float2 om = IN ? make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1]))
+                             : make_float2(__saturatef(hi[2 * pr] - kf), __saturatef(hi[2 * pr + 1] - kf));
+        if (!CLAMP) {
+            if (IN && om.y == 0.0f) ur2.y = ur2.x;
+            if (!IN && om.x == 0.0f) ur2.x = ur2.y;
+        }
+        bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, __fmul2_rn(om, iv2), acc2[pr]);
     }
 }
 
@@ -530,27 +561,26 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             const float kfA = (float)(kA - kbase);
             ViewGeo2 g;
             view_geo2<POLY>(a, x, y, s_cs[slot], s_cs[slotB], zb, zb_lo, kfA, g);
-            if (onA) {
-                const uint32_t colx = (uint32_t)(base + slot * p.slot_floats + min(max(g.ci0 - s_col[slot], 0), p.W - 2)) -
-                                      (0x4B000000u << SH);
-                if (kA > kfull_lo && kA < kfull_hi)
-                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, g.fc.x, g.ur0.x, g.dur.x, rmax, g.inv_v.x, kfA,
-                                                          lo, hi, acc2);
-                else
-                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, g.fc.x, g.ur0.x, g.dur.x, rmax, g.inv_v.x, kfA,
-                                                         lo, hi, acc2);
-            }
-            if (onB) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!(h ? onB : onA)) continue;
+                const int k = kA + h, sl = h ? slotB : slot;
+                const float fc = h ? g.fc.y : g.fc.x, ur0 = h ? g.ur0.y : g.ur0.x, dur = h ? g.dur.y : g.dur.x;
+                const float inv_v = h ? g.inv_v.y : g.inv_v.x, kf = kfA + (float)h;
                 const uint32_t colx =
-                    (uint32_t)(base + slotB * p.slot_floats + min(max(g.ci1 - s_col[slotB], 0), p.W - 2)) -
+                    (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - s_col[sl], 0), p.W - 2)) -
                     (0x4B000000u << SH);
-                const float kfB = kfA + 1.0f;
-                if (kB > kfull_lo && kB < kfull_hi)
-                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, g.fc.y, g.ur0.y, g.dur.y, rmax, g.inv_v.y, kfB,
-                                                          lo, hi, acc2);
+                // full: every slice inside its window with weight 1; ramps: windows
+                // still opening (no slice ended) or closing (every slice started)
+                if (k > kfull_lo && k < kfull_hi)
+                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+                else if (p.mono && k < kfull_hi)
+                    bp_view_ramp<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+                else if (p.mono && k > kfull_lo)
+                    bp_view_ramp<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi,
+                                                               acc2);
                 else
-                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, g.fc.y, g.ur0.y, g.dur.y, rmax, g.inv_v.y, kfB,
-                                                         lo, hi, acc2);
+                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
             }
         }
         __syncwarp();
@@ -677,7 +707,8 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return KATS_OK;
-    BP2Args b{a, W, srows, slot, p.dev_status, (float)(p.dlam / (2.0 * kPi) / (MODE == 0 ? 1.0 : p.g.d_alpha))};
+    BP2Args b{a, W, srows, slot, p.dev_status, (float)(p.dlam / (2.0 * kPi) / (MODE == 0 ? 1.0 : p.g.d_alpha)),
+              p.pi_monotone ? 1 : 0};
     // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
     const bool poly = p.r_fov <= p.g.R * 0.70710678;
     // every contributing row within half a row of the detector (plan extents, FP32 on device)

@@ -37,6 +37,7 @@ struct Plan {
     float *pi_w0 = nullptr, *pi_w1 = nullptr;    // [N][ny][nx]
     int32_t *slice_kmin = nullptr, *slice_kmax = nullptr;  // [N] per table slice
     std::vector<int32_t> h_slice_kmin, h_slice_kmax;       // host copies (view ranges of volume slabs)
+    bool pi_monotone = false;  // window starts / ends nondecreasing in the slice for every voxel column
     float *hk = nullptr;    // Hilbert kernel, [2 n_cols - 2], entry n + n_cols - 2 for n = c - c'
     // Toeplitz operand of the tensor-core Hilbert step: Bt[c][c'] = hk(c - c') for c < n_cols,
     // c' < n_cols - 1 (zero elsewhere), split as hi = value with the low 13 mantissa bits cleared

@@ -357,6 +357,27 @@ __global__ void k_pi_points(DevGeom G, int64_t n, const double *xyz, double *li,
 }
 
 // Per table slice: min k0, max k1, sum of window lengths; and global lambda extents.
+// Clears *flag when some voxel column's window start k0 - w0 or end k1 + w1 (in
+// view units, exact in FP64) decreases from one slice to the next; slice N-1 is
+// followed by slice 0 of the next pitch, one turn (vpt views) later.  The PI
+// window of a point moves monotonically with z along the helix (Sec. II), so the
+// flag stays set up to the tables' rounding; the backprojection then walks only
+// the slices a view reaches.
+__global__ void k_pi_monotone(DevGeom G, const int32_t *k0, const int32_t *k1, const float *w0, const float *w1,
+                              int *flag)
+{
+    const int64_t nxy = G.nx * G.ny, n = G.N * nxy;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / nxy, xy = t % nxy;
+        const bool wrap = j + 1 == G.N;
+        const int64_t tn = wrap ? xy : t + nxy;
+        const double shift = wrap ? (double)G.vpt : 0.0;
+        const double s0 = (double)k0[t] - (double)w0[t], s1 = (double)k0[tn] + shift - (double)w0[tn];
+        const double e0 = (double)k1[t] + (double)w1[t], e1 = (double)k1[tn] + shift + (double)w1[tn];
+        if (s1 < s0 || e1 < e0) *flag = 0;
+    }
+}
+
 __global__ void k_slice_reduce(int64_t nxy, const int32_t *k0, const int32_t *k1, const double *li,
                                const double *lo, int32_t *kmin, int32_t *kmax, unsigned long long *sum,
                                double *lmin_part, double *lmax_part)
@@ -628,10 +649,11 @@ static int build(Plan *p)
     double *lam_i = nullptr, *lam_o = nullptr, *lmin_part = nullptr, *lmax_part = nullptr;
     unsigned long long *sums = nullptr;
     float *ext_part = nullptr;
+    int *mono_flag = nullptr;
     const int ext_blocks = 148 * 8;
     auto cleanup = [&]() {
         for (void *q : {(void *)lam_i, (void *)lam_o, (void *)lmin_part, (void *)lmax_part, (void *)sums,
-                        (void *)ext_part})
+                        (void *)ext_part, (void *)mono_flag})
             if (q) cudaFreeAsync(q, st);
     };
     k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256, 0, st>>>(G, p->kap_idx, p->kap_frac);
@@ -643,6 +665,8 @@ static int build(Plan *p)
     if (e == cudaSuccess) e = dev_malloc_async((void **)&lmax_part, sizeof(double) * N, st);
     if (e == cudaSuccess) e = dev_malloc_async((void **)&sums, sizeof(unsigned long long) * N, st);
     if (e == cudaSuccess) e = dev_malloc_async((void **)&ext_part, sizeof(float) * 4 * ext_blocks, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&mono_flag, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mono_flag, 0xFF, sizeof(int), st);  // nonzero: monotone
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "plan scratch allocation");
@@ -652,7 +676,10 @@ static int build(Plan *p)
     k_slice_reduce<<<(unsigned)N, 256, 0, st>>>(nxy, p->pi_k0, p->pi_k1, lam_i, lam_o, p->slice_kmin,
                                                p->slice_kmax, sums, lmin_part, lmax_part);
     k_extents<<<ext_blocks, 256, 0, st>>>(G, p->pi_k0, p->pi_k1, p->trig, ext_part);
+    k_pi_monotone<<<(unsigned)std::min<int64_t>(ceil_div(N * nxy, 256), 148 * 16), 256, 0, st>>>(
+        G, p->pi_k0, p->pi_k1, p->pi_w0, p->pi_w1, mono_flag);
     e = cudaGetLastError();
+    int mono = 0;
     std::vector<int32_t> kmin(N), kmax(N);
     std::vector<unsigned long long> hs(N);
     std::vector<double> lmin(N), lmax(N);
@@ -664,10 +691,12 @@ static int build(Plan *p)
     if (e == cudaSuccess) e = cudaMemcpyAsync(lmax.data(), lmax_part, sizeof(double) * N, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ext.data(), ext_part, sizeof(float) * 4 * ext_blocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mono, mono_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "plan kernels and reductions");
 
+    p->pi_monotone = mono != 0;
     p->h_slice_kmin = kmin;
     p->h_slice_kmax = kmax;
     // views the whole volume needs; slice s uses table slice s mod N shifted by (s div N) turns
@@ -794,6 +823,7 @@ int katsevich_plan_info(const kats_plan *plan, kats_plan_info *info)
     info->gf_cols = p->gf_cols;
     info->workspace_bytes = katsevich_workspace_bytes(plan, KATS_PREC_FP32);
     info->plan_bytes = (int64_t)p->plan_bytes;
+    info->pi_monotone = p->pi_monotone ? 1 : 0;
     return KATS_OK;
 }
 

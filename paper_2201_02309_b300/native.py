@@ -50,7 +50,7 @@ class kats_plan_info(ctypes.Structure):
                 ("slices_per_pitch", ctypes.c_int64), ("n_psi", ctypes.c_int64),
                 ("first_view", ctypes.c_int64), ("n_filtered_views", ctypes.c_int64),
                 ("update_count", ctypes.c_int64), ("gf_cols", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("plan_bytes", ctypes.c_int64)]
+                ("plan_bytes", ctypes.c_int64), ("pi_monotone", ctypes.c_int64)]
 
 
 class kats_server_config(ctypes.Structure):

@@ -79,6 +79,14 @@ def test_plan_info_c1(c1):
     assert np.allclose([info["alpha_min"], info["alpha_max"]], ext[2:4], rtol=1e-5, atol=1e-7)
     assert np.allclose([info["w_min"], info["w_max"]], ext[4:6], rtol=1e-5, atol=1e-5)
     assert info["alpha_m"] == pytest.approx(oracle.alpha_m(g), rel=1e-15)
+    # window starts / ends nondecreasing slice to slice (FP32 end weights as stored)
+    t = op.pi
+    s0 = t["k0"] - t["w0"].astype(np.float32).astype(np.float64)
+    e0 = t["k1"] + t["w1"].astype(np.float32).astype(np.float64)
+    s0 = np.concatenate([s0, s0[:1] + g["views_per_turn"]], 0)
+    e0 = np.concatenate([e0, e0[:1] + g["views_per_turn"]], 0)
+    mono = bool(np.all(np.diff(s0, axis=0) >= 0) and np.all(np.diff(e0, axis=0) >= 0))
+    assert mono and info["pi_monotone"] == 1
 
 
 def test_pi_endpoints_fp64(kats):

@@ -88,6 +88,30 @@ def test_periodicity(g1):
             assert np.allclose(p0, pk, rtol=1e-11, atol=1e-11)
 
 
+def test_pi_endpoints_increase_with_z(g1):
+    # Along a line parallel to the axis the PI-line's endpoints move up the helix with
+    # the point: l_i(z) and l_o(z) are strictly increasing (the PI window shifts
+    # monotonically, the property the backprojection's window ramps use).  The sweep
+    # spans more than a pitch, so the one-turn jump of the periodic property is crossed.
+    for x in random_points(g1, 12, seed=21):
+        zs = x[2] + np.linspace(-0.7, 0.7, 57) * g1["P"]
+        ends = np.array([oracle.pi_endpoints(g1, x[0], x[1], z) for z in zs])
+        assert np.all(np.diff(ends[:, 0]) > 0) and np.all(np.diff(ends[:, 1]) > 0)
+
+
+def test_pi_table_windows_monotone_in_slice(g1):
+    # the same property on the table: window start k0 - w0 and end k1 + w1 (view
+    # units) never decrease from slice to slice, including slice N-1 -> slice 0 of
+    # the next pitch one turn later
+    t = oracle.pi_table(g1)
+    vpt = g1["views_per_turn"]
+    s = t["k0"] - t["w0"]
+    e = t["k1"] + t["w1"]
+    s = np.concatenate([s, s[:1] + vpt], 0)
+    e = np.concatenate([e, e[:1] + vpt], 0)
+    assert np.all(np.diff(s, axis=0) >= 0) and np.all(np.diff(e, axis=0) >= 0)
+
+
 def test_project_point_matches_acquisition_rays(g1):
     # The ray the acquisition model fires at detector (alpha*, w*) passes through x.
     for x in random_points(g1, 30, seed=11, rmax_frac=0.8):
