@@ -137,19 +137,26 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     const int n_slabs = (int)slab_lo.size() - 1;
     auto chunk_lo = [&](int i) { return nf * i / n_chunks; };
 
-    cudaStream_t cs = nullptr;
-    std::vector<cudaEvent_t> ev((size_t)(n_chunks + n_slabs + 2), nullptr);
+    // copies on cs, filter chunks on fs, backprojection slabs on st: a filter chunk can run
+    // while a slab's last wave of CTAs leaves SMs idle
+    cudaStream_t cs = nullptr, fs = nullptr;
+    // events: [0] start, [1, n_chunks] copies, then slabs, then [.. + n_chunks] filter chunks, last: copies done
+    std::vector<cudaEvent_t> ev((size_t)(2 * n_chunks + n_slabs + 2), nullptr);
+    const size_t ev_filt = (size_t)(1 + n_chunks + n_slabs);
     auto cleanup = [&]() {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);  // released once recorded work completes
         if (cs) cudaStreamDestroy(cs);   // likewise
+        if (fs) cudaStreamDestroy(fs);
     };
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking);
     for (size_t i = 0; e == cudaSuccess && i < ev.size(); ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     int rc = KATS_OK;
-    if (e != cudaSuccess) rc = cuda_fail(e, "copy stream and events");
-    // the copy stream starts after the work already issued on st (e.g. a previous item using ws)
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy / filter streams and events");
+    // both side streams start after the work already issued on st (e.g. a previous item using ws)
     if (!rc && (e = cudaEventRecord(ev[0], st)) == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+    if (!rc && e == cudaSuccess) e = cudaStreamWaitEvent(fs, ev[0], 0);
     for (int i = 0; !rc && e == cudaSuccess && i < n_chunks; ++i) {
         const int64_t v0 = chunk_lo(i), v1 = chunk_lo(i + 1);  // filtered views [v0, v1) need [v0, v1]
         e = cudaMemcpyAsync(d_win + v0 * view, host_sino + (p.first_view + v0) * view,
@@ -165,17 +172,21 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
         while (!rc && e == cudaSuccess && filtered < n_chunks && (j == n_slabs - 1 || chunk_lo(filtered) <= hi)) {
             const int i = filtered++;
             const int64_t v0 = chunk_lo(i), v1 = chunk_lo(i + 1);
-            e = cudaStreamWaitEvent(st, ev[1 + i], 0);
+            e = cudaStreamWaitEvent(fs, ev[1 + i], 0);
             if (e != cudaSuccess) break;
             if (fp32)
                 rc = launch_filter(p, d_win + v0 * view, (float *)rws + v0 * p.g.n_rows * p.gf_cols, fws, fws_bytes,
-                                   st, v1 - v0);
+                                   fs, v1 - v0);
             else
                 rc = launch_filter16(p, precision, d_win + v0 * view,
-                                     (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, st,
+                                     (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, fs,
                                      v1 - v0);
+            if (!rc) e = cudaEventRecord(ev[ev_filt + (size_t)i], fs);
         }
         if (rc || e != cudaSuccess) break;
+        // the slab needs every chunk filtered so far (chunks complete in order on fs)
+        e = cudaStreamWaitEvent(st, ev[ev_filt + (size_t)(filtered - 1)], 0);
+        if (e != cudaSuccess) break;
         rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
                   : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
         if (rc) break;
