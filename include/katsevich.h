@@ -379,6 +379,16 @@ KATS_API int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, doub
                                  double *host_M, void *stream);
 
 /*
+ * Measured read bandwidth of the current GPU's shared-memory data path, the
+ * path the backprojection's bilinear taps are read through (its roofline):
+ * 4 CTAs per SM of 1024 threads stream conflict-free 16-byte shared loads; the
+ * best of 4 timed rounds of 3 launches, in bytes per second, goes to
+ * *bytes_per_second.  Synchronous (its own stream); about 40 ms.  Errors:
+ * KATS_EINVAL for a NULL pointer, KATS_ECUDA.
+ */
+KATS_API int katsevich_smem_read_bandwidth(double *bytes_per_second);
+
+/*
  * Host-side fault injection for tests: the next n device allocations the
  * library makes (plan tables and scratch, a server's arena) fail as if the
  * device were out of memory, without calling CUDA; the call then returns

@@ -26,7 +26,7 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_arena_create", "katsevich_arena_alloc", "katsevich_arena_free",
            "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
            "katsevich_debug_fail_allocs", "katsevich_project", "katsevich_sparse_upsample",
-           "katsevich_noise_workspace_bytes", "katsevich_add_noise"]
+           "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -106,6 +106,7 @@ def load() -> ctypes.CDLL:
         "katsevich_pi_endpoints": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_int64, P, P, P]),
         "katsevich_plan_destroy": (None, [P]),
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+        "katsevich_smem_read_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
         "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
@@ -227,6 +228,13 @@ def katsevich_pi_endpoints(geom: dict, n, xyz_ptr, li_ptr, lo_ptr) -> None:
 
 def katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr) -> None:
     check(load().katsevich_recon_noalloc(plan, sino_ptr, vol_ptr, batch, stream_ptr))
+
+
+def katsevich_smem_read_bandwidth() -> float:
+    """Measured shared-memory read bandwidth of the current GPU, bytes per second."""
+    out = ctypes.c_double(0.0)
+    check(load().katsevich_smem_read_bandwidth(ctypes.byref(out)))
+    return out.value
 
 
 def katsevich_device_status(plan) -> int:

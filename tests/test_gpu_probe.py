@@ -1,0 +1,23 @@
+"""The shared-memory read-bandwidth probe that grounds the backprojection's roofline."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_smem_read_bandwidth_near_unit_count_peak():
+    import torch
+    import paper_2201_02309_b300.native as native
+
+    props = torch.cuda.get_device_properties(0)
+    bw = max(native.katsevich_smem_read_bandwidth() for _ in range(2))
+    # 128 B per clock per SM at the maximum SM clock bounds it from above (a little slack for
+    # timer granularity); half of it from below catches a probe that measures something else
+    derived = props.multi_processor_count * 128 * 2032e6
+    assert 0.5 * derived < bw < 1.05 * derived
+
+
+def test_smem_read_bandwidth_rejects_null():
+    import ctypes
+    import paper_2201_02309_b300.native as native
+
+    assert native.load().katsevich_smem_read_bandwidth(ctypes.POINTER(ctypes.c_double)()) == 1  # KATS_EINVAL
