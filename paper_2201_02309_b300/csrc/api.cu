@@ -126,12 +126,14 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
         return KATS_OK;
     }
     const int n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, nf / 256));
-    // slabs of whole 16-slice z tiles: a small first slab starts backprojecting after few chunks, a
-    // small last slab leaves little to copy back at the end, the middle ones are 64 slices
+    // slabs of whole 16-slice z tiles.  The first four are small: the first starts backprojecting
+    // after a few chunks, and each further 16 slices need only about a chunk more of views, which
+    // arrive faster than a small slab is backprojected, so the GPU is not left waiting for the
+    // copies; the middle slabs are 64 slices, the last small again (little to copy back at the end)
     std::vector<int> slab_lo{0};
     while (slab_lo.back() < nz) {
         const int64_t s0 = slab_lo.back(), left = nz - s0;
-        const int64_t n = s0 == 0 ? 16 : (left <= 80 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 64);
+        const int64_t n = s0 < 64 ? 16 : (left <= 80 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 64);
         slab_lo.push_back((int)std::min<int64_t>(nz, s0 + std::max<int64_t>(n, 1)));
     }
     const int n_slabs = (int)slab_lo.size() - 1;
@@ -169,7 +171,8 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
         int64_t lo, hi;
         slab_views(p, s0, s0 + n, &lo, &hi);
         // filter every chunk up to the one holding the slab's last view
-        while (!rc && e == cudaSuccess && filtered < n_chunks && (j == n_slabs - 1 || chunk_lo(filtered) <= hi)) {
+        auto more = [&]() { return filtered < n_chunks && (j == n_slabs - 1 || chunk_lo(filtered) <= hi); };
+        while (!rc && e == cudaSuccess && more()) {
             const int i = filtered++;
             const int64_t v0 = chunk_lo(i), v1 = chunk_lo(i + 1);
             e = cudaStreamWaitEvent(fs, ev[1 + i], 0);
@@ -182,14 +185,30 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
                                      (uint32_t *)rws + v0 * (p.g.n_rows + 1) * p.gf_cols, fws, fws_bytes, fs,
                                      v1 - v0);
             if (!rc) e = cudaEventRecord(ev[ev_filt + (size_t)i], fs);
+            if (rc || e != cudaSuccess || j > 0) continue;
+            // the first slab takes each chunk's views as soon as they are filtered (partial sums in
+            // the volume, the same order of additions as one launch), so the GPU does not sit idle
+            // while the rest of the slab's views arrive
+            const bool last = !more();
+            BPRange r;
+            r.k_lo = i == 0 ? INT32_MIN : (int)(p.first_view + v0);
+            r.k_hi = last ? INT32_MAX : (int)(p.first_view + v1 - 1);
+            r.acc_in = i > 0;
+            r.acc_final = last;
+            e = cudaStreamWaitEvent(st, ev[ev_filt + (size_t)i], 0);
+            if (e != cudaSuccess) break;
+            rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n, r)
+                      : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n, r);
         }
         if (rc || e != cudaSuccess) break;
-        // the slab needs every chunk filtered so far (chunks complete in order on fs)
-        e = cudaStreamWaitEvent(st, ev[ev_filt + (size_t)(filtered - 1)], 0);
-        if (e != cudaSuccess) break;
-        rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
-                  : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
-        if (rc) break;
+        if (j > 0) {
+            // the slab needs every chunk filtered so far (chunks complete in order on fs)
+            e = cudaStreamWaitEvent(st, ev[ev_filt + (size_t)(filtered - 1)], 0);
+            if (e != cudaSuccess) break;
+            rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
+                      : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
+            if (rc) break;
+        }
         e = cudaEventRecord(ev[1 + n_chunks + j], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[1 + n_chunks + j], 0);
         if (e == cudaSuccess)

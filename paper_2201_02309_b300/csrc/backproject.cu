@@ -39,6 +39,11 @@ struct BPArgs {
     const float2 *trig, *trig_lo;
     int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
     int s_begin, s_end;  // slices [s_begin, s_end) of this launch; s_begin a multiple of the z tile
+    // views [k_lo, k_hi] of this launch (backprojection only).  acc_in: the volume holds the raw
+    // sums of the views below k_lo and the launch continues them; acc_final: scale and store the
+    // result, else store raw sums for a later launch.  A split run adds every view in the order
+    // of one launch, so its result is bit for bit that of one launch.
+    int k_lo, k_hi, acc_in, acc_final;
     int64_t first_view;
     float R, D, x0, y0, dx, dy;
     float alpha0, inv_da, w0row, inv_dw, dz_over_dw, scale;
@@ -121,9 +126,15 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     // z_{s0} - z_src(kmin) in FP64 once; later views subtract h dl (k - kmin)
     float zb, zb_lo;
     z_base(a, s0, kmin, &zb, &zb_lo);
-    int km = ((kmin % a.vpt) + a.vpt) % a.vpt;
+    if (a.acc_in) {
+#pragma unroll
+        for (int t = 0; t < BP_T; ++t)
+            if (s0 + t < a.s_end) acc[t] = a.vol[((int64_t)(s0 + t) * a.ny + iy) * a.nx + ix];
+    }
+    const int kv0 = max(kmin, a.k_lo), kv1 = min(kmax, a.k_hi);
+    int km = ((kv0 % a.vpt) + a.vpt) % a.vpt;
     const int64_t per_view = (int64_t)a.n_rows * a.gcols;
-    for (int k = kmin; k <= kmax; ++k) {
+    for (int k = kv0; k <= kv1; ++k) {
         float u, v;
         view_uv(a, __ldg(a.trig + km), __ldg(a.trig_lo + km), x, y, &u, &v);
         km = (km + 1 == a.vpt) ? 0 : km + 1;
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 #pragma unroll
     for (int t = 0; t < BP_T; ++t) {
         const int s = s0 + t;
-        if (s < a.s_end) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = acc[t] * a.scale;
+        if (s < a.s_end) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = a.acc_final ? acc[t] * a.scale : acc[t];
     }
 }
 
@@ -405,7 +416,9 @@ __device__ __forceinline__ void view_geo2(const BPArgs &a, float x, float y, flo
     g.dur = __fmul2_rn(M, f2(a.dz_over_dw));
 }
 
-template <int PITCH, int MODE, bool POLY, bool ROWS_OK>
+// RANGED: the launch takes a share of the views (BPArgs k_lo .. acc_final); the plain form
+// compiles without that bookkeeping.
+template <int PITCH, int MODE, bool POLY, bool ROWS_OK, bool RANGED>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
@@ -476,14 +489,28 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (active) {
-        atomicMin(&s_K0, kmin);
-        atomicMax(&s_K1, kmax);
+    // views this launch adds (kmin / kmax stay the windows' ends: weights and geometry use them)
+    const int kvmin = RANGED ? max(kmin, a.k_lo) : kmin, kvmax = RANGED ? min(kmax, a.k_hi) : kmax;
+    if (active && kvmin <= kvmax) {
+        atomicMin(&s_K0, kvmin);
+        atomicMax(&s_K1, kvmax);
     }
     __syncthreads();
     const int K0 = s_K0, K1 = s_K1;
-    if (K0 > K1) return;  // no active voxel in this CTA (uniform exit)
-    const int nviews = K1 - K0 + 1;
+    // no view in range: raw sums that stay raw need no store (uniform exit); otherwise the
+    // store below still writes zeros (first launch) or scales the sums (last launch)
+    if (K0 > K1 && (!RANGED || (a.acc_in && !a.acc_final))) return;
+    const int nviews = K0 <= K1 ? K1 - K0 + 1 : 0;
+    if (RANGED && a.acc_in && active && !producer) {
+#pragma unroll
+        for (int t = 0; t < B2_T; ++t) {
+            const int s = s0 + t;
+            if (s < a.s_end) {
+                const float v = a.vol[((int64_t)s * a.ny + iy) * a.nx + ix];
+                if (t & 1) acc2[t >> 1].y = v; else acc2[t >> 1].x = v;
+            }
+        }
+    }
 
     if (producer) {
         // ---------------- producer warp: column window + TMA for each view
@@ -555,8 +582,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
             return;  // the producer's own bounded waits end the CTA
         }
-        const bool onA = active && kA >= kmin && kA <= kmax;
-        const bool onB = hasB && active && kB >= kmin && kB <= kmax;
+        const bool onA = active && kA >= kvmin && kA <= kvmax;
+        const bool onB = hasB && active && kB >= kvmin && kB <= kvmax;
         if (onA || onB) {
             const float kfA = (float)(kA - kbase);
             ViewGeo2 g;
@@ -599,7 +626,10 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 #pragma unroll
     for (int t = 0; t < B2_T; ++t) {
         const int s = s0 + t;
-        if (s < a.s_end) a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = ((t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x) * p.out_scale;
+        if (s < a.s_end) {
+            const float v = (t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x;
+            a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = (!RANGED || a.acc_final) ? v * p.out_scale : v;
+        }
     }
 }
 
@@ -619,6 +649,10 @@ static BPArgs bp_args(const Plan &p)
     a.nz = (int)g.nz;
     a.s_begin = 0;
     a.s_end = (int)g.nz;
+    a.k_lo = INT32_MIN;
+    a.k_hi = INT32_MAX;
+    a.acc_in = 0;
+    a.acc_final = 1;
     a.N = (int)p.N;
     a.vpt = (int)g.views_per_turn;
     a.n_rows = (int)g.n_rows;
@@ -715,8 +749,15 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
     const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
-    auto kern = poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true> : k_backproject_tma<PITCH, MODE, true, false>)
-                     : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true> : k_backproject_tma<PITCH, MODE, false, false>);
+    const bool ranged = a.k_lo != INT32_MIN || a.k_hi != INT32_MAX || a.acc_in || !a.acc_final;
+    auto kern = ranged ? (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, true>
+                                          : k_backproject_tma<PITCH, MODE, true, false, true>)
+                               : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, true>
+                                          : k_backproject_tma<PITCH, MODE, false, false, true>))
+                       : (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, false>
+                                          : k_backproject_tma<PITCH, MODE, true, false, false>)
+                               : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, false>
+                                          : k_backproject_tma<PITCH, MODE, false, false, false>));
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
               (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
@@ -737,13 +778,17 @@ static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W,
 }
 
 int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st, int s_begin,
-                         int s_count)
+                         int s_count, const BPRange &range)
 {
     BPArgs a = bp_args(p);
     if (s_count >= 0) {
         a.s_begin = s_begin;
         a.s_end = std::min(s_begin + s_count, (int)p.g.nz);
     }
+    a.k_lo = range.k_lo;
+    a.k_hi = range.k_hi;
+    a.acc_in = range.acc_in;
+    a.acc_final = range.acc_final;
     a.gF = nullptr;
     a.vol = vol;
     bool launched = false;
@@ -759,13 +804,18 @@ int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vo
     return KATS_OK;
 }
 
-int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st, int s_begin, int s_count)
+int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st, int s_begin, int s_count,
+                       const BPRange &range)
 {
     BPArgs a = bp_args(p);
     if (s_count >= 0) {
         a.s_begin = s_begin;
         a.s_end = std::min(s_begin + s_count, (int)p.g.nz);
     }
+    a.k_lo = range.k_lo;
+    a.k_hi = range.k_hi;
+    a.acc_in = range.acc_in;
+    a.acc_final = range.acc_final;
     a.gF = gF;
     a.vol = vol;
     const int W = window_cols(p);

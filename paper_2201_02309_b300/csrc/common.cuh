@@ -79,9 +79,17 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t filter16_workspace_bytes(const Plan &p);
 int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
                     cudaStream_t st, int64_t nv = -1);
+// A backprojection launch's share of the views: absolute view indices [k_lo, k_hi]; acc_in: vol
+// holds the raw sums of the earlier views; acc_final: the launch scales and stores the result.
+// Launches over consecutive view ranges, the first without acc_in and the last with acc_final,
+// give bit for bit the result of one launch over all views.
+struct BPRange {
+    int k_lo = INT32_MIN, k_hi = INT32_MAX;
+    int acc_in = 0, acc_final = 1;
+};
 // slabs: slices [s_begin, s_begin + s_count), s_begin a multiple of 16 (s_count < 0: every slice)
 int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st, int s_begin = 0,
-                         int s_count = -1);
+                         int s_count = -1, const BPRange &range = BPRange());
 int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, int64_t M, int ldc, cudaStream_t st,
                         bool *done);
 
@@ -91,7 +99,7 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
                   int64_t nv = -1);
 // gF: [p.n_fviews][n_rows][p.gf_cols], view 0 = half-view p.first_view, pad columns zero
 int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st, int s_begin = 0,
-                       int s_count = -1);
+                       int s_count = -1, const BPRange &range = BPRange());
 int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaStream_t st);
 int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes,
                           cudaStream_t st);
