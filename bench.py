@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Katsevich recon GUPS (voxel·views/s), vol/s, p50/p99 latency vs plain FP32"
 UNIT = "GUPS (1e9 voxel-view updates/s)"
-KERNELS_PER_STEP = 4  # deriv+rebin, Toeplitz GEMM, unrebin+cosine, backprojection
 
 
 def parse():
@@ -281,10 +280,12 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = kats.native.katsevich_launch_count()
     e0.record(stream)
     for _ in range(args.steps):
         plan.recon(sino, out=vol, workspace=ws, precision=prec)
     e1.record(stream)
+    launches = kats.native.katsevich_launch_count() - n_launch0  # the library's own count
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -357,7 +358,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
                 "data": "synthetic", "config": describe(cfg, g, info, args.precision), "vol_per_s": world / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -452,6 +453,7 @@ def run_serving(args):
             for k in range(len(protos)):  # plans cached on the device before the stream starts
                 srv.wait(srv.submit(protos[k], sinos[k], vol_view(pool[0], protos[k]), precision=prec))
             t0 = time.perf_counter()
+            n_launch0 = native.katsevich_launch_count()
             i = 0
             while i < n_req or out:
                 now = time.perf_counter() - t0
@@ -479,6 +481,7 @@ def run_serving(args):
                 elif i < n_req:
                     time.sleep(max(0.0, min(0.001, arrivals[i] - now)))
             stats = srv.stats()
+            stats["launches"] = native.katsevich_launch_count() - n_launch0
         return lat, (last_done - first_submit) / 1e3, stats
 
     clocks = Clocks(0)
@@ -509,7 +512,7 @@ def run_serving(args):
                            "note": "one request at a time through katsevich_recon_host (H2D, recon, D2H)"},
             "served_over_plain": (n_req / span_sat) / mu,
         },
-        "gpu_launches": None, "clocks": clk,
+        "gpu_launches": st_sat["launches"], "clocks": clk,
     }
     print(json.dumps(line))
 
@@ -543,6 +546,7 @@ def run_differentiation(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
     clocks = Clocks(0)
     clocks.start()
+    n_launch0 = kats.native.katsevich_launch_count()
     for i in range(args.steps):
         sino.grad = None
         ev[3 * i].record(st)
@@ -551,6 +555,7 @@ def run_differentiation(args):
         vol.backward(cot)
         ev[3 * i + 2].record(st)
     torch.cuda.synchronize()
+    launches = kats.native.katsevich_launch_count() - n_launch0
     clk = clocks.stop()
     fwd = statistics.mean(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps))
     bwd = statistics.mean(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps))
@@ -561,7 +566,7 @@ def run_differentiation(args):
                        "detector_rows_cols": [g["n_rows"], g["n_cols"]], "views_per_turn": g["views_per_turn"],
                        "pitch_mm": g["P"], "updates_per_volume": upd / B},
             "forward_ms": fwd, "backward_ms": bwd, "forward_gups": upd / fwd * 1e-6, "backward_gups": upd / bwd * 1e-6,
-            "gpu_launches": None, "clocks": clk}
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
 
 
@@ -590,6 +595,7 @@ def run_simulate(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * args.steps)]
     clocks = Clocks(0)
     clocks.start()
+    n_launch0 = kats.native.katsevich_launch_count()
     for i in range(args.steps):
         ev[4 * i].record(st)
         g_gt = kats.project(g, vol)
@@ -599,6 +605,7 @@ def run_simulate(args):
         kats.add_noise(g_up, I0=1e5, var=0.5, seed=i)
         ev[4 * i + 3].record(st)
     torch.cuda.synchronize()
+    launches = kats.native.katsevich_launch_count() - n_launch0
     clk = clocks.stop()
     t_proj = statistics.mean(ev[4 * i].elapsed_time(ev[4 * i + 1]) for i in range(args.steps))
     t_up = statistics.mean(ev[4 * i + 1].elapsed_time(ev[4 * i + 2]) for i in range(args.steps))
@@ -610,7 +617,7 @@ def run_simulate(args):
             "data": "synthetic", "config": {"workload": "simulate_" + cfg["name"], "views": g["n_views"],
                                             "keep": 4, "I0": 1e5, "var": 0.5},
             "stages_ms": {"project": t_proj, "sparse_upsample": t_up, "noise": t_noise},
-            "gpu_launches": 4 * args.steps, "clocks": clk}
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
 
 

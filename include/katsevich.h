@@ -389,6 +389,13 @@ KATS_API int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, doub
 KATS_API int katsevich_smem_read_bandwidth(double *bytes_per_second);
 
 /*
+ * Number of kernels the library has launched in this process so far (every
+ * device, every entry point), for launch accounting: the difference across a
+ * region is the library's launches inside it.
+ */
+KATS_API int64_t katsevich_launch_count(void);
+
+/*
  * Host-side fault injection for tests: the next n device allocations the
  * library makes (plan tables and scratch, a server's arena) fail as if the
  * device were out of memory, without calling CUDA; the call then returns

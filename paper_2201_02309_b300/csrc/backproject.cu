@@ -762,6 +762,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
               (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
     kern<<<grid, B2_THREADS, smem, st>>>(map, b);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *launched = true;
     return KATS_OK;
@@ -825,6 +826,7 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
               (unsigned)ceil_div(a.s_end - a.s_begin, BP_T));
     k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
@@ -1143,6 +1145,7 @@ static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, 
     // 1/v* <= 1/(R - r_fov) for every voxel column, rounded up
     const float inv_v_max = (float)(1.0 / (p.g.R - p.r_fov)) * 1.0001f;
     kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, vol, gF);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *launched = true;
     return KATS_OK;
@@ -1167,6 +1170,7 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
     dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
               (unsigned)ceil_div(a.s_end - a.s_begin, BP_T));
     k_backproject_T<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a, vol, gF);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }

@@ -62,6 +62,9 @@ constexpr int kDevStatusTimeout = 1;
 // thread-local error message
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
+// Count of the library's kernel launches in this process (katsevich_launch_count).
+void count_launches(int n);
+int64_t launches_so_far();
 
 #define KATS_CUDA(call)                                                 \
     do {                                                                \

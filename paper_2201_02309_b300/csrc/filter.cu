@@ -211,6 +211,7 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
     if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     kd<<<g1, 256, sm1, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp,
                              a_lam, a_alp, vpb);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
     const int ld4 = (int)p.tc_n;
@@ -224,6 +225,7 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
         }
         dim3 g2((unsigned)ceil_div(nc, GBN), (unsigned)ceil_div(M, GBM));
         k_toeplitz_gemm<<<g2, 256, 0, st>>>(g3, g4, p.hk, M, (int)p.nc1, (int)nc, (int)Kp, ld4, (int)nc, 0);
+        count_launches(1);
         KATS_CUDA(cudaGetLastError());
     }
     dim3 g3d((unsigned)ceil_div(p.gf_cols, 32), (unsigned)ceil_div(nv, vpb));
@@ -234,6 +236,7 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
         KATS_CUDA(cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab3));
     ku<<<g3d, 256, cache3 ? tab3 : 0, st>>>(g4, gF, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np,
                                          (int)p.gf_cols, ld4, vpb);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
@@ -349,6 +352,7 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
     if (sm2 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_rebin_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     k_unrebin_cos_T<<<dim3((unsigned)ceil_div(Kp4, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm1, st>>>(
         gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp4, (int)p.gf_cols);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
     if (ceil_div(M, GBM) > 65535) {
@@ -357,14 +361,17 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
     }
     k_toeplitz_gemm<<<dim3((unsigned)ceil_div(p.nc1, GBN), (unsigned)ceil_div(M, GBM)), 256, 0, st>>>(
         g4a, g3a, p.hk, M, (int)nc, (int)p.nc1, (int)Kp4, (int)Kp, (int)nc, 1);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     k_rebin_T<<<dim3((unsigned)ceil_div(p.nc1, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm2, st>>>(
         g3a, g1a, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     const int64_t total = p.g.n_views * nr * nc;
     k_deriv_T<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
         g1a, sino, p.first_view, nv, p.g.n_views, (int)nr, (int)nc, a_lam, a_alp);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }

@@ -151,6 +151,7 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
     dim3 g1((unsigned)ceil_div(p.tc_k16, 32), (unsigned)ceil_div(nv, vpb));
     kd<<<g1, 256, sm1, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np,
                              (int)p.tc_k16, a_lam, a_alp, scale, vpb);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     bool tc = false;
     int rc = launch_hilbert_tc16(p, prec, g3, g4, M, (int)p.tc_n, st, &tc);
@@ -169,6 +170,7 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
     dim3 g3d((unsigned)ceil_div(p.gf_cols, 32), (unsigned)ceil_div(nv, 8 * vpw));
     ku<<<g3d, 256, cache3 ? tab3 : 0, st>>>(g4, gFp, p.psi_idx, p.psi_frac, p.cosa, nv, (int)nr, (int)nc, (int)np,
                                          (int)p.gf_cols, (int)p.tc_n, vpw);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }

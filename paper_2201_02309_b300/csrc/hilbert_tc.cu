@@ -495,6 +495,7 @@ int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, 
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T16_SMEM));
     dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
     kern<<<grid, TC_THREADS, T16_SMEM, st>>>(mA, mBh, mBl, a);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *done = true;
     return KATS_OK;
@@ -518,6 +519,7 @@ int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int 
     KATS_CUDA(cudaFuncSetAttribute(k_hilbert_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
     k_hilbert_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mBh, mBl, a);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *done = true;
     return KATS_OK;

@@ -28,6 +28,10 @@ int cuda_fail(cudaError_t e, const char *what)
     return (e == cudaErrorMemoryAllocation) ? KATS_ENOMEM : KATS_ECUDA;
 }
 
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
 // Host-side fault injection for tests: the next g_fail_allocs device
 // allocations made through dev_malloc / dev_malloc_async report
 // cudaErrorMemoryAllocation without calling CUDA.
@@ -657,7 +661,9 @@ static int build(Plan *p)
             if (q) cudaFreeAsync(q, st);
     };
     k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256, 0, st>>>(G, p->kap_idx, p->kap_frac);
+    count_launches(1);
     k_plan_psi<<<(unsigned)ceil_div(nr * nc, 128), 128, 0, st>>>(G, p->psi_idx, p->psi_frac);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = dev_malloc_async((void **)&lam_i, sizeof(double) * N * nxy, st);
     if (e == cudaSuccess) e = dev_malloc_async((void **)&lam_o, sizeof(double) * N * nxy, st);
@@ -673,11 +679,15 @@ static int build(Plan *p)
     }
     k_plan_pi<<<(unsigned)ceil_div(N * nxy, 128), 128, 0, st>>>(G, p->pi_k0, p->pi_k1, p->pi_w0, p->pi_w1, lam_i,
                                                                  lam_o);
+    count_launches(1);
     k_slice_reduce<<<(unsigned)N, 256, 0, st>>>(nxy, p->pi_k0, p->pi_k1, lam_i, lam_o, p->slice_kmin,
                                                p->slice_kmax, sums, lmin_part, lmax_part);
+    count_launches(1);
     k_extents<<<ext_blocks, 256, 0, st>>>(G, p->pi_k0, p->pi_k1, p->trig, ext_part);
+    count_launches(1);
     k_pi_monotone<<<(unsigned)std::min<int64_t>(ceil_div(N * nxy, 256), 148 * 16), 256, 0, st>>>(
         G, p->pi_k0, p->pi_k1, p->pi_w0, p->pi_w1, mono_flag);
+    count_launches(1);
     e = cudaGetLastError();
     int mono = 0;
     std::vector<int32_t> kmin(N), kmax(N);
@@ -739,6 +749,8 @@ using namespace kats;
 extern "C" {
 
 const char *katsevich_last_error(void) { return g_err; }
+
+int64_t katsevich_launch_count(void) { return kats::launches_so_far(); }
 
 void katsevich_debug_fail_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
 
@@ -876,6 +888,7 @@ int katsevich_pi_endpoints(const kats_geometry *g, int64_t n, const double *host
     e = cudaMemcpy(d, host_xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_pi_points<<<(unsigned)ceil_div(n, 128), 128>>>(G, n, d, d + 3 * n, d + 4 * n);
+        count_launches(1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(host_lam_i, d + 3 * n, sizeof(double) * n, cudaMemcpyDeviceToHost);

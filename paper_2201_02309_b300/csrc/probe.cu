@@ -60,10 +60,12 @@ extern "C" int katsevich_smem_read_bandwidth(double *bytes_per_second)
     float best = 0.0f;
     for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {  // the first launch warms up
         k_smem_read<<<blocks, threads, 0, st>>>(out, iters);
+        count_launches(1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int k = 0; e == cudaSuccess && k < 3; ++k) {
             k_smem_read<<<blocks, threads, 0, st>>>(out, iters);
+            count_launches(1);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);

@@ -335,6 +335,7 @@ int katsevich_project(const kats_geometry *g, const float *vol, float *sino, int
     P.nv = nv;
     const int64_t rays = nv * g->n_rows * g->n_cols;
     k_project<<<(unsigned)ceil_div(rays, 256), 256, 0, (cudaStream_t)stream>>>(P, vol, sino);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
@@ -349,6 +350,7 @@ int katsevich_sparse_upsample(const kats_geometry *g, const float *sino, float *
     const int64_t n = nv * g->n_rows * g->n_cols;
     k_sparse_upsample<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(sino, out, nv * g->n_rows,
                                                                                    (int)g->n_cols, keep);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     return KATS_OK;
 }
@@ -371,8 +373,10 @@ int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, double I0, do
     unsigned int *M_bits = (unsigned int *)workspace;
     KATS_CUDA(cudaMemsetAsync(M_bits, 0, sizeof(unsigned int), st));
     k_max<<<148 * 4, 256, 0, st>>>(g_up, n, M_bits);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     k_noise<<<148 * 8, 256, 0, st>>>(g_up, g_in, n, I0, mean, sqrt(var), seed, M_bits, counts);
+    count_launches(1);
     KATS_CUDA(cudaGetLastError());
     if (host_M) {
         unsigned int bits = 0;

@@ -26,7 +26,8 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_arena_create", "katsevich_arena_alloc", "katsevich_arena_free",
            "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
            "katsevich_debug_fail_allocs", "katsevich_project", "katsevich_sparse_upsample",
-           "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth"]
+           "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth",
+           "katsevich_launch_count"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -107,6 +108,7 @@ def load() -> ctypes.CDLL:
         "katsevich_plan_destroy": (None, [P]),
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_smem_read_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+        "katsevich_launch_count": (ctypes.c_int64, []),
         "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
@@ -235,6 +237,11 @@ def katsevich_smem_read_bandwidth() -> float:
     out = ctypes.c_double(0.0)
     check(load().katsevich_smem_read_bandwidth(ctypes.byref(out)))
     return out.value
+
+
+def katsevich_launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(load().katsevich_launch_count())
 
 
 def katsevich_device_status(plan) -> int:

@@ -21,3 +21,23 @@ def test_smem_read_bandwidth_rejects_null():
     import paper_2201_02309_b300.native as native
 
     assert native.load().katsevich_smem_read_bandwidth(ctypes.POINTER(ctypes.c_double)()) == 1  # KATS_EINVAL
+
+
+def test_launch_count_per_reconstruction():
+    """One FP32 reconstruction is four launches: derivative + rebinning, the Hilbert
+    contraction, backward rebinning + cosine, backprojection."""
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    import paper_2201_02309_b300.native as native
+    import synth
+
+    plan = kats.Plan(kats.make_geometry(synth.config(1)))
+    sino = torch.rand(plan.sino_shape, device="cuda")
+    plan.recon(sino)
+    torch.cuda.synchronize()
+    n0 = native.katsevich_launch_count()
+    for _ in range(3):
+        plan.recon(sino)
+    torch.cuda.synchronize()
+    assert native.katsevich_launch_count() - n0 == 12
