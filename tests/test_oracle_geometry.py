@@ -171,7 +171,7 @@ def test_fit_pitch_fills_detector_and_envelope(g1, g2):
 
 
 def test_derived_geometry_values():
-    # Survey table of the workloads: alpha_m, pitch, slices per pitch.
+    # The workloads' derived values: alpha_m, pitch, slices per pitch.
     g = oracle.derive_geometry(synth.config(1))
     assert oracle.alpha_m(g) == pytest.approx(math.asin(32 * math.sqrt(2) / 500), rel=1e-15)
     assert g["P"] == 58.0 and oracle.pitch_slices(g) == 58 and g["d_w"] == 2.0
