@@ -30,7 +30,10 @@ size_t filter_workspace_bytes(const Plan &p)
 // n_rows * 32 floats (g2 of one view), plus with CACHED n_psi * 32 (int, float) kappa-table
 // entries.  A block handles 32 columns of consecutive views; CACHED reads its columns' table
 // entries once instead of once per view.
-template <bool CACHED>
+// RT > 0 (n_rows <= 8 RT): a thread keeps its RT rows of views v and v + 1 in registers, carries view
+// v + 1 into the next iteration and loads view v + 2 while the block writes view v's lines, so
+// every sinogram value is read once per block and the loads overlap the stores.
+template <bool CACHED, int RT>
 __global__ void __launch_bounds__(256) k_deriv_rebin(const float *__restrict__ sino, float *__restrict__ g3,
                                                      const int32_t *__restrict__ kap_idx,
                                                      const float *__restrict__ kap_frac, const float *__restrict__ lw,
@@ -50,20 +53,60 @@ __global__ void __launch_bounds__(256) k_deriv_rebin(const float *__restrict__ s
             s_kf[l * 32 + cc] = c < nc1 ? kap_frac[l * nc1 + c] : 0.0f;
         }
     const int vb = blockIdx.y * views_per_block, ve = min(vb + views_per_block, nv);
+    const int64_t vstride = (int64_t)n_rows * n_cols;  // sino points at sinogram view first_view
+    constexpr int RA = RT > 0 ? RT : 1;
+    float ra[RA], rb[RA], rd[RA], re[RA], rl[RA];  // rows warp + 8 i: views v (a, b), v + 1 (d, e); lw
+    if (RT > 0) {
+        const float *p0 = sino + vb * vstride, *p1 = p0 + vstride;
+#pragma unroll
+        for (int i = 0; i < RA; ++i) {
+            const int r = warp + 8 * i;
+            const bool ok = c < nc1 && r < n_rows;
+            ra[i] = ok ? p0[r * n_cols + c] : 0.0f;
+            rb[i] = ok ? p0[r * n_cols + c + 1] : 0.0f;
+            rd[i] = ok ? p1[r * n_cols + c] : 0.0f;
+            re[i] = ok ? p1[r * n_cols + c + 1] : 0.0f;
+            rl[i] = r < n_rows ? lw[r] : 0.0f;
+        }
+    }
     for (int v = vb; v < ve; ++v) {
-        const float *p0 = sino + (int64_t)v * n_rows * n_cols;  // sino points at sinogram view first_view
-        const float *p1 = p0 + (int64_t)n_rows * n_cols;
+        const float *p0 = sino + v * vstride;
+        const float *p1 = p0 + vstride;
         __syncthreads();  // s_g2 of the previous view consumed (first pass: tables written)
-#pragma unroll 4
-        for (int r = warp; r < n_rows; r += 8) {
-            float val = 0.0f;
-            if (c < nc1) {
-                const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
-                const float d = p1[r * n_cols + c], e = p1[r * n_cols + c + 1];
+        if (RT > 0) {
+#pragma unroll
+            for (int i = 0; i < RA; ++i) {
+                const int r = warp + 8 * i;
                 // (dg/dlambda + dg/dalpha) at the cell centre, times D / sqrt(D^2 + w^2)
-                val = lw[r] * (a_lam * ((d - a) + (e - b)) + a_alp * ((b - a) + (e - d)));
+                if (r < n_rows)
+                    s_g2[r * 32 + cc] = c < nc1 ? rl[i] * (a_lam * ((rd[i] - ra[i]) + (re[i] - rb[i])) +
+                                                           a_alp * ((rb[i] - ra[i]) + (re[i] - rd[i])))
+                                                : 0.0f;
             }
-            s_g2[r * 32 + cc] = val;
+            if (v + 1 < ve) {
+                const float *p2 = p1 + vstride;  // view v + 2 <= ve <= nv
+#pragma unroll
+                for (int i = 0; i < RA; ++i) {
+                    const int r = warp + 8 * i;
+                    const bool ok = c < nc1 && r < n_rows;
+                    ra[i] = rd[i];
+                    rb[i] = re[i];
+                    rd[i] = ok ? p2[r * n_cols + c] : 0.0f;
+                    re[i] = ok ? p2[r * n_cols + c + 1] : 0.0f;
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int r = warp; r < n_rows; r += 8) {
+                float val = 0.0f;
+                if (c < nc1) {
+                    const float a = p0[r * n_cols + c], b = p0[r * n_cols + c + 1];
+                    const float d = p1[r * n_cols + c], e = p1[r * n_cols + c + 1];
+                    // (dg/dlambda + dg/dalpha) at the cell centre, times D / sqrt(D^2 + w^2)
+                    val = lw[r] * (a_lam * ((d - a) + (e - b)) + a_alp * ((b - a) + (e - d)));
+                }
+                s_g2[r * 32 + cc] = val;
+            }
         }
         __syncthreads();
         if (c < Kp) {
@@ -206,7 +249,8 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
     const bool cache1 = tab1 <= kCacheMax;
     const int vpb = (int)std::max<int64_t>(8, ceil_div(nv, 65535));  // views per block
     dim3 g1((unsigned)ceil_div(Kp, 32), (unsigned)ceil_div(nv, vpb));
-    auto kd = cache1 ? k_deriv_rebin<true> : k_deriv_rebin<false>;
+    auto kd = nr <= 64 ? (cache1 ? k_deriv_rebin<true, 8> : k_deriv_rebin<false, 8>)
+                       : (cache1 ? k_deriv_rebin<true, 0> : k_deriv_rebin<false, 0>);
     const size_t sm1 = smem1 + (cache1 ? tab1 : 0);
     if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     kd<<<g1, 256, sm1, st>>>(sino, g3, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp,
