@@ -389,6 +389,25 @@ KATS_API int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, doub
 KATS_API int katsevich_smem_read_bandwidth(double *bytes_per_second);
 
 /*
+ * Bounds-checked build (compiled with KATS_DEBUG_CHECKS, libkatsevich_debug.so;
+ * it stands in for a memory checker).  The staged-window kernels verify that
+ * every voxel's detector column lies inside its CTA's staged view window and
+ * that every tap row they read unclamped lies inside the staged rows (the
+ * plan's extents claim both).  A violation sets a bit in a device word
+ * instead of reading outside shared memory: 1 backprojection column, 2
+ * backprojection row, 4 adjoint column, 8 adjoint row.
+ * katsevich_debug_checks_enabled: 1 in the checked build, 0 otherwise.
+ * katsevich_debug_check_flags: synchronises the device, returns the word in
+ * *flags (always 0 in the plain build) and clears it; KATS_EINVAL for NULL.
+ */
+KATS_API int katsevich_debug_checks_enabled(void);
+KATS_API int katsevich_debug_check_flags(int *flags);
+/* Checked build only (a no-op otherwise): stage every view window `cols`
+ * columns narrower than its tile needs, so that the column check fires; taps
+ * stay clamped inside the window, results are wrong, nothing faults.  0 ends it. */
+KATS_API void katsevich_debug_narrow_window(int cols);
+
+/*
  * Number of kernels the library has launched in this process so far (every
  * device, every entry point), for launch accounting: the difference across a
  * region is the library's launches inside it.

@@ -26,33 +26,59 @@ def deps():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "katsevich.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+LIB_DEBUG = os.path.join(LIBDIR, "libkatsevich_debug.so")
+# sources whose kernels carry KATS_DEBUG_CHECKS invariant checks (the bounds-checked build)
+DEBUG_SOURCES = {"backproject.cu"}
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into _lib/libkatsevich.so (relocatable device code off)."""
-    if not force and up_to_date():
-        return LIB
+def _compile(src: str, obj: str, verbose: bool, defines=()) -> None:
+    cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+           "-Xptxas", "-v" if verbose else "-O3", *EXTRA.get(os.path.basename(src), []), *defines,
+           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+    subprocess.check_call(cmd)
+
+
+def _link(lib: str, objs) -> None:
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call([NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"])
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every .cu under csrc/ into _lib/libkatsevich.so (relocatable device code off).
+
+    debug=True also builds _lib/libkatsevich_debug.so: the same objects, except that the sources
+    in DEBUG_SOURCES are compiled with KATS_DEBUG_CHECKS (kernel invariant checks); loaded when
+    KATSEVICH_DEBUG_CHECKS=1."""
     os.makedirs(LIBDIR, exist_ok=True)
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
-    for src in sources():
-        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
-        cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-               "-Xptxas", "-v" if verbose else "-O3", *EXTRA.get(os.path.basename(src), []),
-               "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
-        subprocess.check_call(cmd)
-        objs.append(obj)
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    objs = [os.path.join(objdir, os.path.basename(src)[:-3] + ".o") for src in sources()]
+    if force or not up_to_date(LIB):
+        for src, obj in zip(sources(), objs):
+            _compile(src, obj, verbose)
+        _link(LIB, objs)
+    if not debug:
+        return LIB
+    if force or not up_to_date(LIB_DEBUG):
+        dbgdir = os.path.join(HERE, "_build_debug")
+        os.makedirs(dbgdir, exist_ok=True)
+        dobjs = []
+        for src, obj in zip(sources(), objs):
+            if os.path.basename(src) in DEBUG_SOURCES:
+                obj = os.path.join(dbgdir, os.path.basename(src)[:-3] + ".o")
+                _compile(src, obj, verbose, ["-DKATS_DEBUG_CHECKS"])
+            dobjs.append(obj)
+        _link(LIB_DEBUG, dobjs)
+    return LIB_DEBUG
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

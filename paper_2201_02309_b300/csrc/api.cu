@@ -107,6 +107,7 @@ static void slab_views(const Plan &p, int64_t s0, int64_t s1, int64_t *lo, int64
 // on st after this call waits for all of it.
 int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
 {
+    kats::NvtxRange nvtx_range("katsevich: host item");
     const size_t view = view_elems(p);
     const size_t win = sizeof(float) * (size_t)(p.n_fviews + 1) * view;
     float *d_win = (float *)ws;
@@ -238,6 +239,7 @@ int64_t katsevich_workspace_bytes(const kats_plan *plan, int precision)
 int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int batch, int precision, void *workspace,
                      size_t workspace_bytes, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: filter");
     int rc = check_common(plan, sino, gF, batch, precision, workspace);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
@@ -256,6 +258,7 @@ int katsevich_filter(const kats_plan *plan, const float *sino, float *gF, int ba
 
 int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, int batch, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: backproject");
     if (!plan || !gF || !vol || batch < 1) {
         set_error("bad argument");
         return KATS_EINVAL;
@@ -272,6 +275,7 @@ int katsevich_backproject(const kats_plan *plan, const float *gF, float *vol, in
 int katsevich_recon(const kats_plan *plan, const float *sino, float *vol, int batch, int precision, void *workspace,
                     size_t workspace_bytes, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: recon");
     int rc = check_common(plan, sino, vol, batch, precision, workspace, true);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
@@ -292,6 +296,7 @@ int katsevich_recon(const kats_plan *plan, const float *sino, float *vol, int ba
 int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, float *sino_grad, int batch, int precision,
                       void *workspace, size_t workspace_bytes, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: adjoint");
     int rc = check_common(plan, vol_grad, sino_grad, batch, precision, workspace);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
@@ -314,6 +319,7 @@ int katsevich_adjoint(const kats_plan *plan, const float *vol_grad, float *sino_
 
 int katsevich_backproject_adjoint(const kats_plan *plan, const float *vol, float *gF, int batch, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: backproject adjoint");
     if (!plan || !vol || !gF || batch < 1) {
         set_error("bad argument");
         return KATS_EINVAL;
@@ -330,6 +336,7 @@ int katsevich_backproject_adjoint(const kats_plan *plan, const float *vol, float
 int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, float *sino, int batch, int precision,
                              void *workspace, size_t workspace_bytes, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: filter adjoint");
     int rc = check_common(plan, gF, sino, batch, precision, workspace);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);
@@ -356,6 +363,7 @@ int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int pre
 int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch, int precision,
                          void *workspace, size_t workspace_bytes, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: recon host");
     int rc = check_common(plan, host_sino, host_vol, batch, precision, workspace, true);
     if (rc) return rc;
     const Plan &p = *reinterpret_cast<const Plan *>(plan);

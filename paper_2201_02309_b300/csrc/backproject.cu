@@ -21,12 +21,32 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
 #include "common.cuh"
 
 namespace kats {
+
+// Invariant checks of the staged-window kernels, compiled in with KATS_DEBUG_CHECKS (the
+// bounds-checked build that stands in for a memory checker): bit 1 a backprojection tap column
+// outside the CTA's staged columns, bit 2 an unclamped backprojection tap row outside the staged
+// rows, bit 4 / 8 the same for the adjoint's window.  A violation is recorded, and the access
+// stays inside the window (columns are clamped, rows are in the window's slack), so the checked
+// build never reads outside shared memory.
+__device__ int g_debug_flags = 0;
+
+#ifdef KATS_DEBUG_CHECKS
+#define KATS_DCHECK(ok, bit)                                  \
+    do {                                                      \
+        if (!(ok)) atomicOr(&::kats::g_debug_flags, (bit));   \
+    } while (0)
+#else
+#define KATS_DCHECK(ok, bit) \
+    do {                     \
+    } while (0)
+#endif
 
 constexpr int BP_T = 8;  // slices per thread
 constexpr int BP_BX = 16, BP_BY = 8;
@@ -276,6 +296,8 @@ __device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2
     if (CLAMP) {
         ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
         ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
+    } else {
+        KATS_DCHECK(ur2.x >= 0.0f && ur2.x <= rmax && ur2.y >= 0.0f && ur2.y <= rmax, 2);
     }
     const float2 m1 = make_float2(-1.0f, -1.0f);
     const float2 yv = __fadd2_rd(ur2, make_float2(8388608.0f, 8388608.0f));  // 2^23 + floor(ur)
@@ -594,6 +616,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 const int k = kA + h, sl = h ? slotB : slot;
                 const float fc = h ? g.fc.y : g.fc.x, ur0 = h ? g.ur0.y : g.ur0.x, dur = h ? g.dur.y : g.dur.x;
                 const float inv_v = h ? g.inv_v.y : g.inv_v.x, kf = kfA + (float)h;
+                KATS_DCHECK((h ? g.ci1 : g.ci0) - s_col[sl] >= 0 && (h ? g.ci1 : g.ci0) - s_col[sl] <= p.W - 2, 1);
                 const uint32_t colx =
                     (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - s_col[sl], 0), p.W - 2)) -
                     (0x4B000000u << SH);
@@ -705,6 +728,10 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
+// Checked build only: columns taken off every staged window, so that a test can see the column
+// check fire (the taps stay clamped inside the window, the result is wrong, nothing faults).
+static std::atomic<int> g_debug_narrow{0};
+
 // Staged window width: the tile's columns (B2_TX x B2_TY voxel centres) subtend at
 // most 2 atan(L / 2 d) with L the tile diagonal and d = R - r_fov the nearest
 // source distance; add floor and alignment slack.
@@ -781,6 +808,7 @@ static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W,
 int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st, int s_begin,
                          int s_count, const BPRange &range)
 {
+    kats::NvtxRange nvtx_range("backprojection16 (step 7)");
     BPArgs a = bp_args(p);
     if (s_count >= 0) {
         a.s_begin = s_begin;
@@ -793,7 +821,7 @@ int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vo
     a.gF = nullptr;
     a.vol = vol;
     bool launched = false;
-    const int W = window_cols(p);
+    const int W = std::max(4, window_cols(p) - g_debug_narrow.load());
     int rc = prec == KATS_PREC_FP16 ? launch_tma_any<2>(p, a, gFp, W, st, &launched)
                                     : launch_tma_any<1>(p, a, gFp, W, st, &launched);
     if (rc) return rc;
@@ -808,6 +836,7 @@ int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vo
 int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t st, int s_begin, int s_count,
                        const BPRange &range)
 {
+    kats::NvtxRange nvtx_range("backprojection (step 7)");
     BPArgs a = bp_args(p);
     if (s_count >= 0) {
         a.s_begin = s_begin;
@@ -819,7 +848,7 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
     a.acc_final = range.acc_final;
     a.gF = gF;
     a.vol = vol;
-    const int W = window_cols(p);
+    const int W = std::max(4, window_cols(p) - g_debug_narrow.load());
     bool launched = false;
     int rc = launch_tma_any<0>(p, a, gF, W, st, &launched);
     if (rc || launched) return rc;
@@ -1052,6 +1081,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
             int ci;
             float fc;
             column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
+            KATS_DCHECK(ci - s_col[j % 3] >= 0 && ci - s_col[j % 3] <= W - 2, 4);
             const uint32_t colx = (uint32_t)(2 * b * slot_floats + min(max(ci - s_col[j % 3], 0), W - 2)) -
                                   (0x4B000000u << SH);
             const float M = a.D * rsqrtf(fmaf(u, u, v * v));
@@ -1072,6 +1102,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 if (wv == 0.0f) continue;
                 float ur = fmaf((float)t, dur, ur0);
                 if (!ROWS_OK) ur = fminf(fmaxf(ur, 0.0f), rmax);
+                else KATS_DCHECK(ur >= 0.0f && ur <= rmax, 8);
                 const float yv = __fadd_rd(ur, 8388608.0f);
                 const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
                 const float fr = ur - (yv - 8388608.0f);
@@ -1157,7 +1188,7 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
     a.gF = gF;
     a.vol = nullptr;
     KATS_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)(p.n_fviews * p.g.n_rows * p.gf_cols), st));
-    const int W = window_cols(p);
+    const int W = std::max(4, window_cols(p) - g_debug_narrow.load());
     bool launched = false;
     int rc = KATS_OK;
     if (W <= 32)
@@ -1176,3 +1207,40 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
 }
 
 }  // namespace kats
+
+extern "C" {
+
+int katsevich_debug_checks_enabled(void)
+{
+#ifdef KATS_DEBUG_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+void katsevich_debug_narrow_window(int cols)
+{
+#ifdef KATS_DEBUG_CHECKS
+    kats::g_debug_narrow.store(cols > 0 ? cols : 0);
+#else
+    (void)cols;
+#endif
+}
+
+int katsevich_debug_check_flags(int *flags)
+{
+    if (!flags) {
+        kats::set_error("bad argument");
+        return KATS_EINVAL;
+    }
+    KATS_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    KATS_CUDA(cudaMemcpyFromSymbol(&v, kats::g_debug_flags, sizeof(int)));
+    const int zero = 0;
+    KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_flags, &zero, sizeof(int)));
+    *flags = v;
+    return KATS_OK;
+}
+
+}  // extern "C"

@@ -10,6 +10,8 @@
 
 #include "../../include/katsevich.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace kats {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
@@ -62,6 +64,16 @@ constexpr int kDevStatusTimeout = 1;
 // thread-local error message
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
+// NVTX range for the host-side span of one stage (plan, filter, backprojection, ...): what a
+// profiler shows on the CPU timeline and what `ncu --nvtx --nvtx-include` filters on.  NVTX is
+// header-only and costs a few tens of nanoseconds when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Count of the library's kernel launches in this process (katsevich_launch_count).
 void count_launches(int n);
 int64_t launches_so_far();

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(256) k_unrebin_cos(const float *__restrict__ g
 int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st,
                   int64_t nv_chunk)
 {
+    kats::NvtxRange nvtx_range("filter (steps 1-6)");
     const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
     const int64_t Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
     if (ws_bytes < filter_workspace_bytes(p)) {

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(256) k_unrebin_cos16(const float *__restrict__
 int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
                     cudaStream_t st, int64_t nv_chunk)
 {
+    kats::NvtxRange nvtx_range("filter16 (steps 1-6)");
     const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
     const int64_t nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi, M = nv * np;
     if (ws_bytes < filter16_workspace_bytes(p)) {

@@ -775,6 +775,7 @@ int katsevich_fit_pitch(const kats_geometry *g, double factor, double *pitch_out
 
 int katsevich_plan(const kats_geometry *g, kats_plan **out)
 {
+    kats::NvtxRange nvtx_range("katsevich: plan");
     if (!out) {
         set_error("null output pointer");
         return KATS_EINVAL;

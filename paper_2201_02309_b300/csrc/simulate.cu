@@ -301,6 +301,7 @@ extern "C" {
 
 int katsevich_project(const kats_geometry *g, const float *vol, float *sino, int64_t v0, int64_t nv, void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: project");
     int rc = check_geometry_sizes(g);
     if (rc) return rc;
     if (!vol || !sino || v0 < 0 || nv < 1 || v0 + nv > g->n_views) {
@@ -343,6 +344,7 @@ int katsevich_project(const kats_geometry *g, const float *vol, float *sino, int
 int katsevich_sparse_upsample(const kats_geometry *g, const float *sino, float *out, int64_t nv, int keep,
                               void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: sparse upsample");
     if (!g || !sino || !out || nv < 1 || keep < 1 || g->n_rows < 1 || g->n_cols < 1) {
         set_error("sparse_upsample: null buffer or non-positive sizes");
         return KATS_EINVAL;
@@ -361,6 +363,7 @@ int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, double I0, do
                         uint64_t seed, int64_t *counts, void *workspace, size_t workspace_bytes, double *host_M,
                         void *stream)
 {
+    kats::NvtxRange nvtx_range("katsevich: add noise");
     if (!g_up || !g_in || n < 1 || !(I0 > 0) || !(var >= 0) || !workspace) {
         set_error("add_noise: null buffer, n < 1, I0 <= 0 or var < 0");
         return KATS_EINVAL;

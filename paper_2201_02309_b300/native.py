@@ -7,7 +7,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libkatsevich.so")
+# KATSEVICH_DEBUG_CHECKS=1 loads the bounds-checked build (paper_2201_02309_b300.build.build(debug=True))
+LIB_PATH = os.path.join(HERE, "_lib", "libkatsevich_debug.so" if os.environ.get("KATSEVICH_DEBUG_CHECKS") == "1"
+                        else "libkatsevich.so")
 
 KATS_OK, KATS_EINVAL, KATS_EGEOM, KATS_ENOMEM, KATS_ECUDA, KATS_ETIMEOUT, KATS_ESPACE = range(7)
 KATS_PREC_FP32, KATS_PREC_BF16, KATS_PREC_FP16 = 0, 1, 2
@@ -27,7 +29,8 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
            "katsevich_debug_fail_allocs", "katsevich_project", "katsevich_sparse_upsample",
            "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth",
-           "katsevich_launch_count"]
+           "katsevich_launch_count", "katsevich_debug_checks_enabled", "katsevich_debug_check_flags",
+           "katsevich_debug_narrow_window"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -109,6 +112,9 @@ def load() -> ctypes.CDLL:
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_smem_read_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
         "katsevich_launch_count": (ctypes.c_int64, []),
+        "katsevich_debug_checks_enabled": (ctypes.c_int, []),
+        "katsevich_debug_check_flags": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
+        "katsevich_debug_narrow_window": (None, [ctypes.c_int]),
         "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
@@ -242,6 +248,23 @@ def katsevich_smem_read_bandwidth() -> float:
 def katsevich_launch_count() -> int:
     """Kernels the library has launched in this process so far."""
     return int(load().katsevich_launch_count())
+
+
+def katsevich_debug_checks_enabled() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().katsevich_debug_checks_enabled())
+
+
+def katsevich_debug_check_flags() -> int:
+    """Invariant-violation bits recorded by the bounds-checked build (read and cleared)."""
+    out = ctypes.c_int(0)
+    check(load().katsevich_debug_check_flags(ctypes.byref(out)))
+    return out.value
+
+
+def katsevich_debug_narrow_window(cols: int) -> None:
+    """Checked build only: stage view windows `cols` columns too narrow (0 ends it)."""
+    load().katsevich_debug_narrow_window(int(cols))
 
 
 def katsevich_device_status(plan) -> int:
