@@ -100,11 +100,13 @@ static void slab_views(const Plan &p, int64_t s0, int64_t s1, int64_t *lo, int64
 // One item from host buffers, stream-ordered and asynchronous: copy the view
 // window the volume needs, steps 1-7, copy the volume back.  ws holds
 // host_item_bytes(p, precision) bytes.  For windows of 128 MiB and more the
-// copies overlap the kernels: the window arrives in chunks on a second stream; a slab of slices is
-// backprojected as soon as the chunks holding its views are filtered (the PI
-// windows rise with z), while later chunks are still arriving; each slab of
-// the volume is copied back while later slabs are backprojected.  Work issued
-// on st after this call waits for all of it.
+// copies overlap the kernels: the window arrives in chunks on a copy stream and
+// each chunk is filtered on a filter stream as it lands; a slab of slices is
+// backprojected on st once the chunks holding its views are filtered (the PI
+// windows rise with z), the first slab chunk by chunk from partial sums, while
+// later chunks are still arriving; each slab of the volume is copied back
+// while later slabs are backprojected.  Work issued on st after this call
+// waits for all of it.
 int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
 {
     kats::NvtxRange nvtx_range("katsevich: host item");

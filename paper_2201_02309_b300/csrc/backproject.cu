@@ -9,11 +9,14 @@
 // w* is affine in z, so the per-view geometry (trig, atan, rsqrt) is computed
 // once per view and reused by the thread's T slices.
 //
-// k_backproject_tma (main path): a CTA owns a 16 x 16 column tile and 8
+// k_backproject_tma (main path): a CTA owns a 16 x 16 column tile and 16
 // slices.  For each view a producer warp copies its detector window (all rows
 // plus zero rows above and below, a column range covering the tile's
 // projection) into a ring of shared-memory slots by TMA; eight consumer warps
 // read every bilinear tap as a plain shared-memory load with no bounds test.
+// Where a thread's slice windows are opening or closing it visits only the
+// slices the view reaches (the windows move monotonically with z), and a
+// launch may take a range of the views and continue raw sums of earlier ones.
 // k_backproject (fallback for windows TMA cannot stage): the same arithmetic
 // with bounds-tested loads from global memory.
 #include <cuda.h>
@@ -32,9 +35,8 @@ namespace kats {
 // Invariant checks of the staged-window kernels, compiled in with KATS_DEBUG_CHECKS (the
 // bounds-checked build that stands in for a memory checker): bit 1 a backprojection tap column
 // outside the CTA's staged columns, bit 2 an unclamped backprojection tap row outside the staged
-// rows, bit 4 / 8 the same for the adjoint's window.  A violation is recorded, and the access
-// stays inside the window (columns are clamped, rows are in the window's slack), so the checked
-// build never reads outside shared memory.
+// rows, bit 4 / 8 the same for the adjoint's window.  A violation is recorded and the access is
+// clamped into the window, so the checked build never touches shared memory outside it.
 __device__ int g_debug_flags = 0;
 
 #ifdef KATS_DEBUG_CHECKS
@@ -297,7 +299,13 @@ __device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2
         ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
         ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
     } else {
-        KATS_DCHECK(ur2.x >= 0.0f && ur2.x <= rmax && ur2.y >= 0.0f && ur2.y <= rmax, 2);
+#ifdef KATS_DEBUG_CHECKS
+        if (!(ur2.x >= 0.0f && ur2.x <= rmax && ur2.y >= 0.0f && ur2.y <= rmax)) {
+            atomicOr(&g_debug_flags, 2);
+            ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
+            ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
+        }
+#endif
     }
     const float2 m1 = make_float2(-1.0f, -1.0f);
     const float2 yv = __fadd2_rd(ur2, make_float2(8388608.0f, 8388608.0f));  // 2^23 + floor(ur)
@@ -1102,7 +1110,12 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 if (wv == 0.0f) continue;
                 float ur = fmaf((float)t, dur, ur0);
                 if (!ROWS_OK) ur = fminf(fmaxf(ur, 0.0f), rmax);
-                else KATS_DCHECK(ur >= 0.0f && ur <= rmax, 8);
+#ifdef KATS_DEBUG_CHECKS
+                else if (!(ur >= 0.0f && ur <= rmax)) {
+                    atomicOr(&g_debug_flags, 8);
+                    ur = fminf(fmaxf(ur, 0.0f), rmax);
+                }
+#endif
                 const float yv = __fadd_rd(ur, 8388608.0f);
                 const uint32_t q = colx + ((uint32_t)__float_as_int(yv) << SH);
                 const float fr = ur - (yv - 8388608.0f);

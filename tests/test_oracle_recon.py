@@ -1,7 +1,5 @@
 """Whole-operator pins of the oracle: reconstruction of analytic phantoms,
 linearity, and a brute-force check that the adjoint is the exact transpose."""
-import math
-
 import numpy as np
 import pytest
 from scipy.ndimage import binary_erosion
