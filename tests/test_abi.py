@@ -74,3 +74,17 @@ def test_null_arguments(lib):
     lib.katsevich_plan_destroy(None)
     h = ctypes.c_void_p()
     assert lib.katsevich_plan(None, ctypes.byref(h)) == native.KATS_EINVAL
+
+
+def test_measurement_and_debug_entry_points_host_side(lib):
+    """The measurement and checked-build entry points answer on the host: NULL outputs are
+    KATS_EINVAL, the plain build reports no checks (narrowing is a no-op there), and the
+    launch counter is a non-negative count."""
+    assert lib.katsevich_smem_read_bandwidth(None) == native.KATS_EINVAL
+    assert lib.katsevich_debug_check_flags(None) == native.KATS_EINVAL
+    assert native.katsevich_debug_checks_enabled() is False
+    native.katsevich_debug_narrow_window(8)
+    native.katsevich_debug_narrow_window(0)
+    n0 = native.katsevich_launch_count()
+    assert isinstance(n0, int) and n0 >= 0
+    assert native.katsevich_launch_count() == n0  # nothing launched in between
