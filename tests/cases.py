@@ -72,3 +72,15 @@ def c3_small_case():
     cfg.update(nx=64, ny=64, nz=16, turns=2)
     g = oracle.derive_geometry(cfg)
     return cfg, g
+
+
+def tall_case():
+    """A detector of 264 rows and 33 columns: 528 kappa lines and 264 rows are more
+    table entries than the rebinning kernels keep in shared memory, and more rows
+    than the staged backprojection window holds, so the uncached table reads and
+    the global-memory backprojection run."""
+    cfg = dict(R=300.0, D=600.0, views_per_turn=64, turns=3, n_rows=264, n_cols=33, n_cols_full=33, col_keep=1,
+               det_half_width=8.0, nx=12, ny=12, nz=10, voxel=1.0, pitch_factor=1.0)
+    g = oracle.derive_geometry(cfg)
+    sino = np.random.default_rng(9).normal(size=(g["n_views"], g["n_rows"], g["n_cols"]))
+    return cfg, g, sino.astype(np.float32)

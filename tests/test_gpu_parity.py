@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import c1_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2
+from cases import c1_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2, tall_case
 
 pytestmark = pytest.mark.gpu
 
@@ -167,6 +167,22 @@ def test_odd_geometry_batch(kats, torch):
     got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     for b in range(2):
         assert rel_l2(got[b], op.adjoint(y[b].astype(np.float64))) < TOL
+
+
+def test_tall_detector_uncached_tables(kats, torch):
+    _, g, sino = tall_case()
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    assert kp.info["n_psi"] == 528
+    compare_tables(kp, op)
+    vol = kp.recon(torch.from_numpy(sino).cuda()).cpu().numpy()
+    assert rel_l2(vol, op.recon(sino.astype(np.float64))) < TOL
+    y = np.random.default_rng(2).normal(size=kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel_l2(got, op.adjoint(y.astype(np.float64))) < TOL
+    # the reduced-precision backprojection needs the staged window: refused, not wrong
+    with pytest.raises(kats.KatsevichError) as e:
+        kp.recon(torch.from_numpy(sino).cuda(), precision=kats.KATS_PREC_FP16)
+    assert e.value.status == kats.native.KATS_EINVAL
 
 
 def test_narrow_detector_fallback_path(kats, torch):
