@@ -10,16 +10,19 @@
 // (the dropped A_lo T_lo term is ~2^-22 of the product).  T_hi / T_lo are
 // plan constants; A is split in place in shared memory.
 //
-// One CTA computes a 128 x 256 tile of C in TMEM:
+// A 128 x 256 tile of C accumulates in TMEM.  A persistent CTA per SM walks its
+// tiles with two accumulators, so one tile's epilogue overlaps the next tile's MMAs:
 //   warp 0      TMA producer (A tile 128 x 32, T_hi / T_lo tiles 256 x 32,
-//               fp32, 128-byte swizzle), 2-stage ring
+//               fp32, 128-byte swizzle), 2-stage ring running across tiles
 //   warp 1      TMEM allocation and the single-thread tcgen05.mma issuer
-//   warps 2..5  split A into hi / lo in shared memory, then the epilogue
-//               (tcgen05.ld -> registers -> global g4)
+//   warps 2..5  split A into hi / lo in shared memory
+//   warps 6..9  the epilogue (tcgen05.ld -> registers -> global g4)
 // Every mbarrier wait is bounded; on a timeout the CTA records a device
-// status, drains its own copies and frees TMEM before returning.
+// status, lets its MMAs finish and its copies land, and frees TMEM before
+// returning.
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -32,16 +35,11 @@ constexpr int TC_M = 128, TC_N = 256, TC_K = 32;  // tile; K block = one 128-byt
 constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_M * TC_K * 4;  // 16 KB
-constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 4;  // 32 KB
-constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // A, A_lo, T_hi, T_lo
-constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;       // + alignment slack
 constexpr int kTcWaitLimit = 1 << 22;
 
-// Instruction descriptor, kind::tf32: D fp32 (bits 4-5 = 1), A and B tf32
+// Instruction descriptor fields, kind::tf32: D fp32 (bits 4-5 = 1), A and B tf32
 // (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                                ((uint32_t)(TC_M >> 4) << 24);
+// 17-22, M >> 4 at bits 24-28 (TpShape::IDESC).
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -93,13 +91,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
+template <uint32_t IDESC>
+__device__ __forceinline__ void mma_tf32_n(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(kIdescTf32), "r"(accumulate)
+        "l"(da), "l"(db), "r"(IDESC), "r"(accumulate)
         : "memory");
 }
 
@@ -137,38 +136,71 @@ struct TcArgs {
     int *status;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// Steps of Eq. (HF) as above: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (n-tile fastest), with two TMEM accumulators (2 x 256
+// columns), so that the epilogue of one tile overlaps the MMAs of the next and the
+// TMA / split / MMA ring runs on across tiles without refilling.
+//   warp 0      TMA producer        warp 1      TMEM allocation, MMA issuer
+//   warps 2..5  A split hi / lo     warps 6..9  epilogue (TMEM -> registers -> g4)
+// Every wait is bounded; on a timeout the CTA records a device status, lets its
+// issued MMAs finish and its copies land, and frees TMEM before returning.
+constexpr int TP_THREADS = 320;
+constexpr int TP_N = 256, TP_STAGES = 2;  // tile width and ring depth of the launched form
+
+// Tile TC_M x N, STAGES-deep ring; one stage holds A, A_lo (TC_M x TC_K) and T_hi, T_lo (N x TC_K).
+template <int N, int STAGES>
+struct TpShape {
+    static constexpr uint32_t B_BYTES = N * TC_K * 4;
+    static constexpr uint32_t STAGE_BYTES = 2 * TC_A_BYTES + 2 * B_BYTES;
+    static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+    // kind::tf32 instruction descriptor for TC_M x N
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                      ((uint32_t)(TC_M >> 4) << 24);
+};
+
+template <int N, int STAGES>
+__global__ void __launch_bounds__(TP_THREADS, 1)
     k_hilbert_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
-                 const __grid_constant__ CUtensorMap mapBl, TcArgs a)
+                   const __grid_constant__ CUtensorMap mapBl, TcArgs a, int n_ntiles, int64_t n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    __shared__ __align__(8) uint64_t s_full[TC_STAGES], s_conv[TC_STAGES], s_empty[TC_STAGES], s_acc;
+    using SH = TpShape<N, STAGES>;
+    __shared__ __align__(8) uint64_t s_full[STAGES], s_conv[STAGES], s_empty[STAGES];
+    __shared__ __align__(8) uint64_t s_accf[2], s_acce[2], s_done;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort, s_issued;
+    __shared__ int s_abort;
+    __shared__ long long s_issued;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (saddr(tc_raw) + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
     unsigned char *const gbase = tc_raw + (base - saddr(tc_raw));
-    const int64_t m0 = (int64_t)blockIdx.y * TC_M;
-    const int n0 = blockIdx.x * TC_N;
-    auto stA = [&](int s) { return base + (uint32_t)s * TC_STAGE_BYTES; };
+    auto stA = [&](int s) { return base + (uint32_t)s * SH::STAGE_BYTES; };
     auto stAlo = [&](int s) { return stA(s) + TC_A_BYTES; };
     auto stBh = [&](int s) { return stA(s) + 2 * TC_A_BYTES; };
-    auto stBl = [&](int s) { return stA(s) + 2 * TC_A_BYTES + TC_B_BYTES; };
+    auto stBl = [&](int s) { return stA(s) + 2 * TC_A_BYTES + SH::B_BYTES; };
+    const int nkb = a.kblocks;
+    const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_m0 = [&](int64_t i) { return ((int64_t)blockIdx.x + i * gridDim.x) / n_ntiles * TC_M; };
+    auto tile_n0 = [&](int64_t i) { return (int)(((int64_t)blockIdx.x + i * gridDim.x) % n_ntiles) * N; };
+    auto aborted = [&]() { return *(volatile int *)&s_abort != 0; };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             bar_init(&s_full[s], 1);
             bar_init(&s_conv[s], 4);
             bar_init(&s_empty[s], 1);
         }
-        bar_init(&s_acc, 1);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&s_accf[b], 1);
+            bar_init(&s_acce[b], 4);
+        }
+        bar_init(&s_done, 1);
         s_abort = 0;
         s_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
-                     "r"((uint32_t)TC_N)
+                     "r"((uint32_t)(2 * N))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -176,114 +208,152 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
-    const int nkb = a.kblocks;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: k-block g of the CTA's sequence goes to stage g % 2
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb & 1;
-                if (kb >= TC_STAGES && !bar_wait(&s_empty[s], (uint32_t)(((kb >> 1) - 1) & 1))) {
-                    atomicExch(&s_abort, 1);
-                    break;
+            long long g = 0;
+            for (int64_t i = 0; i < my_tiles && !aborted(); ++i) {
+                const int64_t m0 = tile_m0(i);
+                const int n0 = tile_n0(i);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (g >= STAGES && !bar_wait(&s_empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
+                        atomicExch(&s_abort, 1);
+                        break;
+                    }
+                    if (aborted()) break;
+                    bar_expect(&s_full[s], TC_A_BYTES + 2 * SH::B_BYTES);
+                    tma_2d(stA(s), &mapA, &s_full[s], kb * TC_K, (int)m0);
+                    tma_2d(stBh(s), &mapBh, &s_full[s], kb * TC_K, n0);
+                    tma_2d(stBl(s), &mapBl, &s_full[s], kb * TC_K, n0);
+                    s_issued = g + 1;
                 }
-                if (*(volatile int *)&s_abort) break;
-                bar_expect(&s_full[s], TC_A_BYTES + 2 * TC_B_BYTES);
-                tma_2d(stA(s), &mapA, &s_full[s], kb * TC_K, (int)m0);
-                tma_2d(stBh(s), &mapBh, &s_full[s], kb * TC_K, n0);
-                tma_2d(stBl(s), &mapBl, &s_full[s], kb * TC_K, n0);
-                s_issued = kb + 1;
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: tile i accumulates in TMEM columns (i % 2) * 256
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb & 1;
-                if (!bar_wait(&s_conv[s], (uint32_t)((kb >> 1) & 1))) {
+            long long g = 0;
+            for (int64_t i = 0; i < my_tiles; ++i) {
+                const int b = (int)(i & 1);
+                if (i >= 2 && !bar_wait(&s_acce[b], (uint32_t)(((i >> 1) - 1) & 1))) {
                     atomicExch(&s_abort, 1);
                     break;
                 }
-                if (*(volatile int *)&s_abort) break;
+                if (aborted()) break;
                 fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * N);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (!bar_wait(&s_conv[s], (uint32_t)((g / STAGES) & 1))) {
+                        atomicExch(&s_abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    if (aborted()) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
 #pragma unroll
-                for (int kk = 0; kk < TC_K / 8; ++kk) {  // 8 tf32 = 32 bytes per MMA
-                    const uint32_t off = (uint32_t)kk * 32u;
-                    const uint64_t dA = sw128_desc(stA(s) + off), dAl = sw128_desc(stAlo(s) + off);
-                    const uint64_t dBh = sw128_desc(stBh(s) + off), dBl = sw128_desc(stBl(s) + off);
-                    mma_tf32(tmem, dA, dBh, (kb | kk) != 0);
-                    mma_tf32(tmem, dA, dBl, 1u);
-                    mma_tf32(tmem, dAl, dBh, 1u);
+                    for (int kk = 0; kk < TC_K / 8; ++kk) {  // 8 tf32 = 32 bytes per MMA
+                        const uint32_t off = (uint32_t)kk * 32u;
+                        const uint64_t dA = sw128_desc(stA(s) + off), dAl = sw128_desc(stAlo(s) + off);
+                        const uint64_t dBh = sw128_desc(stBh(s) + off), dBl = sw128_desc(stBl(s) + off);
+                        mma_tf32_n<SH::IDESC>(acc, dA, dBh, (kb | kk) != 0);
+                        mma_tf32_n<SH::IDESC>(acc, dA, dBl, 1u);
+                        mma_tf32_n<SH::IDESC>(acc, dAl, dBh, 1u);
+                    }
+                    mma_commit(&s_empty[s]);  // stage s free once these MMAs have read it
                 }
-                mma_commit(&s_empty[s]);  // stage s free once these MMAs have read it
+                if (!ok) break;
+                mma_commit(&s_accf[b]);  // tile i complete in buffer b
             }
-            mma_commit(&s_acc);  // accumulator complete (or abandoned on abort)
+            mma_commit(&s_done);  // every MMA this thread issued has completed
+        }
+    } else if (warp < 6) {
+        // ---------------- converters: split A into hi / lo in shared memory
+        const int ct = threadIdx.x - 64;  // 0..127
+        long long g = 0;
+        for (int64_t i = 0; i < my_tiles && !aborted(); ++i) {
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!bar_wait(&s_full[s], (uint32_t)((g / STAGES) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (aborted()) break;
+                float4 *A = reinterpret_cast<float4 *>(gbase + (stA(s) - base));
+                float4 *L = reinterpret_cast<float4 *>(gbase + (stAlo(s) - base));
+#pragma unroll
+                for (int q = 0; q < (int)(TC_A_BYTES / 16) / 128; ++q) {
+                    const int e = ct + 128 * q;
+                    float4 v = A[e], h, l;
+                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                    l.x = v.x - h.x;
+                    l.y = v.y - h.y;
+                    l.z = v.z - h.z;
+                    l.w = v.w - h.w;
+                    A[e] = h;
+                    L[e] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+                __syncwarp();
+                if (lane == 0) bar_arrive(&s_conv[s]);
+            }
         }
     } else {
-        // ---------------- converters (warps 2..5), then epilogue
-        const int ct = threadIdx.x - 64;  // 0..127
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb & 1;
-            if (!bar_wait(&s_full[s], (uint32_t)((kb >> 1) & 1))) {
+        // ---------------- epilogue: TMEM lane = tile row; warp w reads lanes 32 (w % 4) .. + 31
+        const int quarter = warp & 3;
+        for (int64_t i = 0; i < my_tiles; ++i) {
+            const int b = (int)(i & 1);
+            if (!bar_wait(&s_accf[b], (uint32_t)((i >> 1) & 1))) {
                 atomicExch(&s_abort, 1);
                 break;
             }
-            if (*(volatile int *)&s_abort) break;
-            // element-wise split, independent of the swizzled layout: hi in place, lo alongside
-            float4 *A = reinterpret_cast<float4 *>(gbase + (stA(s) - base));
-            float4 *L = reinterpret_cast<float4 *>(gbase + (stAlo(s) - base));
-#pragma unroll
-            for (int i = 0; i < (int)(TC_A_BYTES / 16) / 128; ++i) {
-                const int e = ct + 128 * i;
-                float4 v = A[e], h, l;
-                h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                l.x = v.x - h.x;
-                l.y = v.y - h.y;
-                l.z = v.z - h.z;
-                l.w = v.w - h.w;
-                A[e] = h;
-                L[e] = l;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
-            __syncwarp();
-            if (lane == 0) bar_arrive(&s_conv[s]);
-        }
-        // epilogue: TMEM lane = tile row; warp w may read lanes 32 (w % 4) .. + 31
-        const bool done = bar_wait(&s_acc, 0u);
-        if (!done) atomicExch(&s_abort, 1);
-        fence_after();
-        if (done && !*(volatile int *)&s_abort) {
-            const int quarter = warp & 3;
-            const int64_t row = m0 + quarter * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
-            for (int cb = 0; cb < TC_N / 32; ++cb) {
+            if (aborted()) break;
+            fence_after();
+            const int64_t row = tile_m0(i) + quarter * 32 + lane;
+            const int n0 = tile_n0(i);
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * N);
+            for (int cb = 0; cb < N / 32; ++cb) {
                 float v[32];
                 tmem_ld32(taddr + (uint32_t)(cb * 32), v);
                 if (row < a.M) {
                     float4 *out = reinterpret_cast<float4 *>(a.C + row * a.ldc + n0 + cb * 32);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int q = 0; q < 8; ++q)
+                        out[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&s_acce[b]);  // buffer b free for tile i + 2
         }
     }
 
     // ---------------- teardown
     fence_before();
     __syncthreads();
-    if (s_abort && threadIdx.x == 0) {
-        // drain the producer's copies (the last TC_STAGES issued) before shared memory is released
-        for (int kb = max(0, s_issued - TC_STAGES); kb < s_issued; ++kb)
-            bar_wait(&s_full[kb & 1], (uint32_t)((kb >> 1) & 1));
-        atomicExch(a.status, kDevStatusTimeout);
+    if (threadIdx.x == 0) {
+        const bool done = bar_wait(&s_done, 0u);  // no MMA may still use TMEM when it is freed
+        if (s_abort || !done) {
+            // let the producer's copies (the last STAGES issued) land before shared memory is released
+            for (long long g = s_issued > STAGES ? s_issued - STAGES : 0; g < s_issued; ++g)
+                bar_wait(&s_full[g % STAGES], (uint32_t)((g / STAGES) & 1));
+            atomicExch(a.status, kDevStatusTimeout);
+        }
     }
+    __syncthreads();
     if (warp == 1) {
         __syncwarp();
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * N))
                      : "memory");
     }
 }
@@ -508,17 +578,23 @@ int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int 
 {
     *done = false;
     EncodeFn enc = encoder();
-    if (!enc || M < 1 || ldc % TC_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
-        (reinterpret_cast<uintptr_t>(g4) % 16) != 0 || ceil_div(M, TC_M) > 65535)
+    if (!enc || M < 1 || ldc % TP_N != 0 || p.tc_n % TP_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(g4) % 16) != 0)
         return KATS_OK;
     CUtensorMap mA, mBh, mBl;
-    if (!encode_2d(enc, &mA, g3, p.tc_k, M, TC_K, TC_M) || !encode_2d(enc, &mBh, p.bt_hi, p.tc_k, p.tc_n, TC_K, TC_N) ||
-        !encode_2d(enc, &mBl, p.bt_lo, p.tc_k, p.tc_n, TC_K, TC_N))
+    if (!encode_2d(enc, &mA, g3, p.tc_k, M, TC_K, TC_M) || !encode_2d(enc, &mBh, p.bt_hi, p.tc_k, p.tc_n, TC_K, TP_N) ||
+        !encode_2d(enc, &mBl, p.bt_lo, p.tc_k, p.tc_n, TC_K, TP_N))
         return KATS_OK;
     TcArgs a{g4, M, ldc, (int)(p.tc_k / TC_K), p.dev_status};
-    KATS_CUDA(cudaFuncSetAttribute(k_hilbert_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
-    k_hilbert_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mBh, mBl, a);
+    using SH = TpShape<TP_N, TP_STAGES>;
+    auto kern = k_hilbert_tc<TP_N, TP_STAGES>;
+    KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM));
+    int dev = 0, sms = 0;
+    KATS_CUDA(cudaGetDevice(&dev));
+    KATS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int n_ntiles = (int)(p.tc_n / TP_N);
+    const int64_t n_tiles = (int64_t)n_ntiles * ceil_div(M, TC_M);
+    kern<<<(unsigned)std::min<int64_t>(sms, n_tiles), TP_THREADS, SH::SMEM, st>>>(mA, mBh, mBl, a, n_ntiles, n_tiles);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *done = true;
