@@ -394,7 +394,8 @@ bool encode_2d(EncodeFn enc, CUtensorMap *map, const float *ptr, int64_t inner, 
 // in bf16 / fp16, the Toeplitz operand is split hi + lo in the same type, and
 //     C = A T_hi + A T_lo
 // accumulates in FP32 in TMEM.  Warps: 0 TMA producer, 1 MMA issuer, 2..5
-// epilogue; K blocks of 64 elements (one 128-byte swizzle span).
+// epilogue; K blocks of 64 elements (one 128-byte swizzle span); persistent with
+// two accumulators like the FP32 form.
 constexpr int T16_K = 64;
 constexpr uint32_t T16_A_BYTES = TC_M * T16_K * 2;  // 16 KB
 constexpr uint32_t T16_B_BYTES = TC_N * T16_K * 2;  // 32 KB
@@ -419,36 +420,47 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t d
         : "memory");
 }
 
+// Persistent like k_hilbert_tc: one CTA per SM walks the tiles (n-tile fastest) with two
+// TMEM accumulators; warps 2..5 drain tile i while the MMAs of tile i + 1 run.
 template <bool FP16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_hilbert_tc16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
-                   const __grid_constant__ CUtensorMap mapBl, TcArgs a)
+                   const __grid_constant__ CUtensorMap mapBl, TcArgs a, int n_ntiles, int64_t n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    __shared__ __align__(8) uint64_t s_full[TC_STAGES], s_empty[TC_STAGES], s_acc;
+    __shared__ __align__(8) uint64_t s_full[TC_STAGES], s_empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t s_accf[2], s_acce[2], s_done;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort, s_issued;
+    __shared__ int s_abort;
+    __shared__ long long s_issued;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (saddr(tc_raw) + 1023u) & ~1023u;
-    const int64_t m0 = (int64_t)blockIdx.y * TC_M;
-    const int n0 = blockIdx.x * TC_N;
     auto stA = [&](int s) { return base + (uint32_t)s * T16_STAGE_BYTES; };
     auto stBh = [&](int s) { return stA(s) + T16_A_BYTES; };
     auto stBl = [&](int s) { return stA(s) + T16_A_BYTES + T16_B_BYTES; };
+    const int nkb = a.kblocks;
+    const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_m0 = [&](int64_t i) { return ((int64_t)blockIdx.x + i * gridDim.x) / n_ntiles * TC_M; };
+    auto tile_n0 = [&](int64_t i) { return (int)(((int64_t)blockIdx.x + i * gridDim.x) % n_ntiles) * TC_N; };
+    auto aborted = [&]() { return *(volatile int *)&s_abort != 0; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             bar_init(&s_full[s], 1);
             bar_init(&s_empty[s], 1);
         }
-        bar_init(&s_acc, 1);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&s_accf[b], 1);
+            bar_init(&s_acce[b], 4);
+        }
+        bar_init(&s_done, 1);
         s_abort = 0;
         s_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
-                     "r"((uint32_t)TC_N)
+                     "r"((uint32_t)(2 * TC_N))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -456,77 +468,116 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
-    const int nkb = a.kblocks;
 
     if (warp == 0) {
+        // ---------------- TMA producer: k-block g of the CTA's sequence goes to stage g % 2
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb & 1;
-                if (kb >= TC_STAGES && !bar_wait(&s_empty[s], (uint32_t)(((kb >> 1) - 1) & 1))) {
-                    atomicExch(&s_abort, 1);
-                    break;
+            long long g = 0;
+            for (int64_t i = 0; i < my_tiles && !aborted(); ++i) {
+                const int64_t m0 = tile_m0(i);
+                const int n0 = tile_n0(i);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g & 1);
+                    if (g >= TC_STAGES && !bar_wait(&s_empty[s], (uint32_t)(((g >> 1) - 1) & 1))) {
+                        atomicExch(&s_abort, 1);
+                        break;
+                    }
+                    if (aborted()) break;
+                    bar_expect(&s_full[s], T16_A_BYTES + 2 * T16_B_BYTES);
+                    tma_2d(stA(s), &mapA, &s_full[s], kb * T16_K, (int)m0);
+                    tma_2d(stBh(s), &mapBh, &s_full[s], kb * T16_K, n0);
+                    tma_2d(stBl(s), &mapBl, &s_full[s], kb * T16_K, n0);
+                    s_issued = g + 1;
                 }
-                if (*(volatile int *)&s_abort) break;
-                bar_expect(&s_full[s], T16_A_BYTES + 2 * T16_B_BYTES);
-                tma_2d(stA(s), &mapA, &s_full[s], kb * T16_K, (int)m0);
-                tma_2d(stBh(s), &mapBh, &s_full[s], kb * T16_K, n0);
-                tma_2d(stBl(s), &mapBl, &s_full[s], kb * T16_K, n0);
-                s_issued = kb + 1;
             }
         }
     } else if (warp == 1) {
+        // ---------------- MMA issuer: tile i accumulates in TMEM columns (i % 2) * 256
         if (lane == 0) {
             const uint32_t idesc = idesc_f16<FP16>();
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb & 1;
-                if (!bar_wait(&s_full[s], (uint32_t)((kb >> 1) & 1))) {
+            long long g = 0;
+            for (int64_t i = 0; i < my_tiles; ++i) {
+                const int b = (int)(i & 1);
+                if (i >= 2 && !bar_wait(&s_acce[b], (uint32_t)(((i >> 1) - 1) & 1))) {
                     atomicExch(&s_abort, 1);
                     break;
                 }
-                if (*(volatile int *)&s_abort) break;
+                if (aborted()) break;
                 fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * TC_N);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g & 1);
+                    if (!bar_wait(&s_full[s], (uint32_t)((g >> 1) & 1))) {
+                        atomicExch(&s_abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    if (aborted()) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
 #pragma unroll
-                for (int kk = 0; kk < T16_K / 16; ++kk) {  // 16 elements = 32 bytes per MMA
-                    const uint32_t off = (uint32_t)kk * 32u;
-                    const uint64_t dA = sw128_desc(stA(s) + off);
-                    mma_f16(tmem, dA, sw128_desc(stBh(s) + off), idesc, (kb | kk) != 0);
-                    mma_f16(tmem, dA, sw128_desc(stBl(s) + off), idesc, 1u);
+                    for (int kk = 0; kk < T16_K / 16; ++kk) {  // 16 elements = 32 bytes per MMA
+                        const uint32_t off = (uint32_t)kk * 32u;
+                        const uint64_t dA = sw128_desc(stA(s) + off);
+                        mma_f16(acc, dA, sw128_desc(stBh(s) + off), idesc, (kb | kk) != 0);
+                        mma_f16(acc, dA, sw128_desc(stBl(s) + off), idesc, 1u);
+                    }
+                    mma_commit(&s_empty[s]);  // stage s free once these MMAs have read it
                 }
-                mma_commit(&s_empty[s]);
+                if (!ok) break;
+                mma_commit(&s_accf[b]);  // tile i complete in buffer b
             }
-            mma_commit(&s_acc);
+            mma_commit(&s_done);  // every MMA this thread issued has completed
         }
     } else {
-        const bool done = bar_wait(&s_acc, 0u);
-        if (!done) atomicExch(&s_abort, 1);
-        fence_after();
-        if (done && !*(volatile int *)&s_abort) {
-            const int quarter = warp & 3;
-            const int64_t row = m0 + quarter * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+        // ---------------- epilogue: TMEM lane = tile row; warp w reads lanes 32 (w % 4) .. + 31
+        const int quarter = warp & 3;
+        for (int64_t i = 0; i < my_tiles; ++i) {
+            const int b = (int)(i & 1);
+            if (!bar_wait(&s_accf[b], (uint32_t)((i >> 1) & 1))) {
+                atomicExch(&s_abort, 1);
+                break;
+            }
+            if (aborted()) break;
+            fence_after();
+            const int64_t row = tile_m0(i) + quarter * 32 + lane;
+            const int n0 = tile_n0(i);
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TC_N);
             for (int cb = 0; cb < TC_N / 32; ++cb) {
                 float v[32];
                 tmem_ld32(taddr + (uint32_t)(cb * 32), v);
                 if (row < a.M) {
                     float4 *out = reinterpret_cast<float4 *>(a.C + row * a.ldc + n0 + cb * 32);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) out[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int q = 0; q < 8; ++q)
+                        out[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&s_acce[b]);  // buffer b free for tile i + 2
         }
     }
 
+    // ---------------- teardown
     fence_before();
     __syncthreads();
-    if (s_abort && threadIdx.x == 0) {
-        for (int kb = max(0, s_issued - TC_STAGES); kb < s_issued; ++kb)
-            bar_wait(&s_full[kb & 1], (uint32_t)((kb >> 1) & 1));
-        atomicExch(a.status, kDevStatusTimeout);
+    if (threadIdx.x == 0) {
+        const bool done = bar_wait(&s_done, 0u);  // no MMA may still use TMEM when it is freed
+        if (s_abort || !done) {
+            for (long long g = s_issued > TC_STAGES ? s_issued - TC_STAGES : 0; g < s_issued; ++g)
+                bar_wait(&s_full[g & 1], (uint32_t)((g >> 1) & 1));
+            atomicExch(a.status, kDevStatusTimeout);
+        }
     }
+    __syncthreads();
     if (warp == 1) {
         __syncwarp();
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * TC_N))
                      : "memory");
     }
 }
@@ -552,8 +603,8 @@ int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, 
     *done = false;
     EncodeFn enc = encoder();
     const int kind = prec == KATS_PREC_FP16 ? 1 : 0;
-    if (!enc || M < 1 || ldc % TC_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
-        (reinterpret_cast<uintptr_t>(g4) % 16) != 0 || ceil_div(M, TC_M) > 65535)
+    if (!enc || M < 1 || ldc % TC_N != 0 || p.tc_n % TC_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(g4) % 16) != 0)
         return KATS_OK;
     CUtensorMap mA, mBh, mBl;
     if (!encode_2d_u16(enc, &mA, g3, p.tc_k16, M, T16_K, TC_M) ||
@@ -563,8 +614,12 @@ int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, 
     TcArgs a{g4, M, ldc, (int)(p.tc_k16 / T16_K), p.dev_status};
     auto kern = kind ? k_hilbert_tc16<true> : k_hilbert_tc16<false>;
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T16_SMEM));
-    dim3 grid((unsigned)(p.tc_n / TC_N), (unsigned)ceil_div(M, TC_M));
-    kern<<<grid, TC_THREADS, T16_SMEM, st>>>(mA, mBh, mBl, a);
+    int dev = 0, sms = 0;
+    KATS_CUDA(cudaGetDevice(&dev));
+    KATS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int n_ntiles = (int)(p.tc_n / TC_N);
+    const int64_t n_tiles = (int64_t)n_ntiles * ceil_div(M, TC_M);
+    kern<<<(unsigned)std::min<int64_t>(sms, n_tiles), TC_THREADS, T16_SMEM, st>>>(mA, mBh, mBl, a, n_ntiles, n_tiles);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *done = true;
