@@ -208,8 +208,13 @@ KATS_API int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, fl
 /*
  * End-to-end call with HOST buffers: copies the needed sinogram views from
  * host_sino (pinned memory recommended) to the device, runs katsevich_recon and
- * copies the volume back to host_vol, all on `stream`, then waits for the
- * stream.  `workspace` (device) must hold katsevich_host_workspace_bytes.
+ * copies the volume back to host_vol, then waits for `stream`.  `workspace`
+ * (device) must hold katsevich_host_workspace_bytes.  Items whose view window
+ * is 128 MiB or more overlap the copies with the kernels on internal streams
+ * (ordered after the work already on `stream`): the window arrives in chunks
+ * that are filtered as they land, slabs of slices are backprojected as soon as
+ * their views are filtered, and finished slabs are copied back while later
+ * ones run.  The volume is bit for bit that of katsevich_recon.
  */
 KATS_API int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision);
 KATS_API int katsevich_recon_host(const kats_plan *plan, const float *host_sino, float *host_vol, int batch,
