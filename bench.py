@@ -319,12 +319,18 @@ def run_ours(args):
         smem_peak = 148 * 128 * sm_mhz * 1e6 / 1e9  # GB/s
         alg_bytes = info["update_count"] * bytes_per_update
         achieved = alg_bytes / (t_bp / 1e3) / 1e9
-        # the same path's read bandwidth measured on this GPU (conflict-free 16-byte shared loads)
+        # the same path's read bandwidth measured on this GPU (conflict-free 16-byte shared loads), and
+        # the hardware bilinear texture-fetch rate a texture-based gather would be bound by
         smem_measured = kats.native.katsevich_smem_read_bandwidth() / 1e9
+        tex32 = kats.native.katsevich_tex_bilinear_rate(False)
+        tex16 = kats.native.katsevich_tex_bilinear_rate(True)
+        updates_per_s = info["update_count"] / (t_bp / 1e3)
         roofline = {"kernel": "k_backproject_tma", "bound": "alu", "achieved": achieved, "peak": smem_peak,
                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("k_backproject_tma"),
                     "peak_source": f"shared-memory data path: 148 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk_kind} clock)",
                     "peak_measured": smem_measured, "frac_of_measured": achieved / smem_measured,
+                    "tex_bilinear_gsamples_per_s": {"fp32": tex32 / 1e9, "fp16": tex16 / 1e9},
+                    "updates_over_tex_fp32": updates_per_s / tex32,
                     "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": t_bp, "filter_ms": t_filter}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region

@@ -394,6 +394,17 @@ KATS_API int katsevich_add_noise(const float *g_up, float *g_in, int64_t n, doub
 KATS_API int katsevich_smem_read_bandwidth(double *bytes_per_second);
 
 /*
+ * Measured rate of bilinear (hardware-filtered) 2-D texture fetches on the
+ * current GPU, FP32 texels (half_texels = 0) or FP16 texels (1): the gather
+ * path a texture-based backprojection would take, one filtered sample per
+ * voxel-view update (with 8-bit interpolation weights).  8 CTAs per SM of 256
+ * threads fetch from a 256 x 256 texture; the best of 4 timed rounds of 3
+ * launches, in samples per second, goes to *samples_per_second.  Synchronous;
+ * about 50 ms.  Errors: KATS_EINVAL for a NULL pointer, KATS_ECUDA.
+ */
+KATS_API int katsevich_tex_bilinear_rate(int half_texels, double *samples_per_second);
+
+/*
  * Bounds-checked build (compiled with KATS_DEBUG_CHECKS, libkatsevich_debug.so;
  * it stands in for a memory checker).  The staged-window kernels verify that
  * every voxel's detector column lies inside its CTA's staged view window and

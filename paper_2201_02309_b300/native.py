@@ -29,6 +29,7 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_arena_largest_free", "katsevich_arena_in_use", "katsevich_arena_destroy",
            "katsevich_debug_fail_allocs", "katsevich_project", "katsevich_sparse_upsample",
            "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth",
+           "katsevich_tex_bilinear_rate",
            "katsevich_launch_count", "katsevich_debug_checks_enabled", "katsevich_debug_check_flags",
            "katsevich_debug_narrow_window"]
 
@@ -111,6 +112,7 @@ def load() -> ctypes.CDLL:
         "katsevich_plan_destroy": (None, [P]),
         "katsevich_recon_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_smem_read_bandwidth": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+        "katsevich_tex_bilinear_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "katsevich_launch_count": (ctypes.c_int64, []),
         "katsevich_debug_checks_enabled": (ctypes.c_int, []),
         "katsevich_debug_check_flags": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
@@ -242,6 +244,13 @@ def katsevich_smem_read_bandwidth() -> float:
     """Measured shared-memory read bandwidth of the current GPU, bytes per second."""
     out = ctypes.c_double(0.0)
     check(load().katsevich_smem_read_bandwidth(ctypes.byref(out)))
+    return out.value
+
+
+def katsevich_tex_bilinear_rate(half_texels: bool = False) -> float:
+    """Measured bilinear texture-fetch rate of the current GPU, samples per second."""
+    out = ctypes.c_double(0.0)
+    check(load().katsevich_tex_bilinear_rate(1 if half_texels else 0, ctypes.byref(out)))
     return out.value
 
 

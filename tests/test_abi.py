@@ -81,6 +81,7 @@ def test_measurement_and_debug_entry_points_host_side(lib):
     KATS_EINVAL, the plain build reports no checks (narrowing is a no-op there), and the
     launch counter is a non-negative count."""
     assert lib.katsevich_smem_read_bandwidth(None) == native.KATS_EINVAL
+    assert lib.katsevich_tex_bilinear_rate(0, None) == native.KATS_EINVAL
     assert lib.katsevich_debug_check_flags(None) == native.KATS_EINVAL
     assert native.katsevich_debug_checks_enabled() is False
     native.katsevich_debug_narrow_window(8)

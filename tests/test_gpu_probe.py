@@ -41,3 +41,12 @@ def test_launch_count_per_reconstruction():
         plan.recon(sino)
     torch.cuda.synchronize()
     assert native.katsevich_launch_count() - n0 == 12
+
+
+def test_tex_bilinear_rate_plausible():
+    import paper_2201_02309_b300.native as native
+
+    for half in (False, True):
+        r = native.katsevich_tex_bilinear_rate(half)
+        # between one filtered sample per SM per 4 clocks and 64 per SM per clock at 2 GHz
+        assert 148 * 0.25 * 1e9 < r < 148 * 64 * 2.1e9, (half, r)
