@@ -141,3 +141,29 @@ def test_injected_allocation_failures(kats):
         assert rs["status"] == 0
         assert np.array_equal(vol.numpy(), alone(kats, torch, g, pinned_sino(torch, g, 9), kats.KATS_PREC_FP32))
     native.katsevich_debug_fail_allocs(0)
+
+
+def test_large_requests_take_the_overlapped_path_in_the_mix(kats):
+    """Requests whose view window is 128 MiB or more run the overlapped host path
+    (chunked copies, filter stream, chunk-by-chunk first slab) inside the server,
+    concurrently with small ones; each result equals the same request run alone."""
+    import torch
+    from paper_2201_02309_b300.serving import Server
+    big = dict(synth.config(2))
+    big.update(nx=64, ny=64, nz=48)
+    gb = kats.make_geometry(big)
+    pb = kats.Plan(gb)
+    assert (pb.info["n_filtered_views"] + 1) * gb["n_rows"] * gb["n_cols"] * 4 >= (128 << 20)
+    gs = kats.make_geometry(mix_configs()[1])
+    reqs = [(gb, kats.KATS_PREC_FP32, 201), (gs, kats.KATS_PREC_FP32, 202), (gb, kats.KATS_PREC_FP16, 203),
+            (gs, kats.KATS_PREC_BF16, 204)]
+    with Server(arena_bytes=4 * block_bytes(kats, gb, kats.KATS_PREC_FP32), plan_cache_bytes=1 << 32, slots=3,
+                max_bypass=4) as srv:
+        sinos = [pinned_sino(torch, g, seed) for g, _, seed in reqs]
+        tickets = [srv.submit(g, s, precision=p) for (g, p, _), s in zip(reqs, sinos)]
+        results = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["max_running"] >= 2, st
+    for (g, p, seed), (vol, rs) in zip(reqs, results):
+        assert rs["status"] == 0
+        assert np.array_equal(vol.numpy(), alone(kats, torch, g, pinned_sino(torch, g, seed), p)), (g["nx"], p)
