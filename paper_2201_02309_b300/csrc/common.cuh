@@ -46,6 +46,10 @@ struct Plan {
     // (exact in TF32) and lo = value - hi; [tc_n][tc_k] row-major.
     float *bt_hi = nullptr, *bt_lo = nullptr;
     int64_t tc_k = 0, tc_n = 0;  // K padded to 32, N padded to 256
+    // the transpose's operand (adjoint of the Hilbert step): Bt'[c'][c] = hk(c - c') for c' < n_cols - 1,
+    // c < n_cols, split the same way; [tct_n][tct_k], tct_n = n_cols - 1 padded to 256, tct_k = n_cols to 32
+    float *btT_hi = nullptr, *btT_lo = nullptr;
+    int64_t tct_k = 0, tct_n = 0;
     // the same operand for the 16-bit Hilbert step: value = hi + lo with hi, lo
     // in bf16 (resp. fp16), [tc_n][tc_k16], K padded to 64
     uint16_t *bt16_hi[2] = {nullptr, nullptr}, *bt16_lo[2] = {nullptr, nullptr};  // [0] bf16, [1] fp16
@@ -121,6 +125,10 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
 size_t filter_workspace_bytes(const Plan &p);
 // tensor-core Hilbert step (hilbert_tc.cu); *done = false when it cannot run
 int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done);
+// C[M][ldc] = A[M][K] . B on the tensor cores (3xTF32), B given as hi / lo [N][K] row-major, K a multiple
+// of 32, N and ldc multiples of 256; *done = false when the tensor-core path cannot run.
+int launch_hilbert_tc_op(const Plan &p, const float *A, int64_t M, int64_t K, const float *b_hi, const float *b_lo,
+                         int64_t N, float *C, int ldc, cudaStream_t st, bool *done);
 size_t filter_adjoint_workspace_bytes(const Plan &p);
 
 // one item from host buffers (api.cu): device bytes it needs, and the

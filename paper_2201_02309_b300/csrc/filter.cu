@@ -290,10 +290,10 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
 size_t filter_adjoint_workspace_bytes(const Plan &p)
 {
     const int64_t nv = p.n_fviews;
-    // region 1: g4^T [v][psi][Kp4], later reused for g1^T [v][row][nc1]; region 2: g3^T [v][psi][Kp]
-    const int64_t Kp4 = (p.g.n_cols + 15) / 16 * 16;
-    const int64_t r1 = std::max<int64_t>(p.n_psi * Kp4, p.g.n_rows * p.nc1);
-    return sizeof(float) * (size_t)(nv * r1 + nv * p.n_psi * kpad(p));
+    // region 1: g4^T [v][psi][tct_k], later reused for g1^T [v][row][nc1]; region 2: g3^T [v][psi][tct_n]
+    // (rows padded to the tensor-core transpose's K and N)
+    const int64_t r1 = std::max<int64_t>(p.n_psi * p.tct_k, p.g.n_rows * p.nc1);
+    return sizeof(float) * (size_t)(nv * r1 + nv * p.n_psi * p.tct_n);
 }
 
 // 6^T then 5^T: g4a[v][l][c] = sum_r cos(alpha_c) gF[v][r][c] * (tap weight of l)
@@ -382,8 +382,8 @@ __global__ void k_deriv_T(const float *__restrict__ g1a, float *__restrict__ sin
 
 int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes, cudaStream_t st)
 {
-    const int64_t nv = p.n_fviews, Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
-    const int64_t Kp4 = (nc + 15) / 16 * 16;
+    const int64_t nv = p.n_fviews, nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
+    const int64_t Kp4 = p.tct_k, Kp = p.tct_n;  // row strides of g4^T and g3^T
     if (ws_bytes < filter_adjoint_workspace_bytes(p)) {
         set_error("filter adjoint workspace too small");
         return KATS_ESPACE;
@@ -400,14 +400,20 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     const int64_t M = nv * np;
-    if (ceil_div(M, GBM) > 65535) {
-        set_error("too many filtered views for one launch (%lld)", (long long)nv);
-        return KATS_EINVAL;
+    // 4^T: the transposed Toeplitz contraction, on the tensor cores when they can run it
+    bool tc = false;
+    int rc = launch_hilbert_tc_op(p, g4a, M, p.tct_k, p.btT_hi, p.btT_lo, p.tct_n, g3a, (int)p.tct_n, st, &tc);
+    if (rc) return rc;
+    if (!tc) {
+        if (ceil_div(M, GBM) > 65535) {
+            set_error("too many filtered views for one launch (%lld)", (long long)nv);
+            return KATS_EINVAL;
+        }
+        k_toeplitz_gemm<<<dim3((unsigned)ceil_div(p.nc1, GBN), (unsigned)ceil_div(M, GBM)), 256, 0, st>>>(
+            g4a, g3a, p.hk, M, (int)nc, (int)p.nc1, (int)Kp4, (int)Kp, (int)nc, 1);
+        count_launches(1);
+        KATS_CUDA(cudaGetLastError());
     }
-    k_toeplitz_gemm<<<dim3((unsigned)ceil_div(p.nc1, GBN), (unsigned)ceil_div(M, GBM)), 256, 0, st>>>(
-        g4a, g3a, p.hk, M, (int)nc, (int)p.nc1, (int)Kp4, (int)Kp, (int)nc, 1);
-    count_launches(1);
-    KATS_CUDA(cudaGetLastError());
     k_rebin_T<<<dim3((unsigned)ceil_div(p.nc1, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm2, st>>>(
         g3a, g1a, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp);
     count_launches(1);

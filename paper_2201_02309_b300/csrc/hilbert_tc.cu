@@ -626,34 +626,41 @@ int launch_hilbert_tc16(const Plan &p, int prec, const uint16_t *g3, float *g4, 
     return KATS_OK;
 }
 
-// g4[M][ldc] = g3[M][tc_k] . T on the tensor cores (ldc a multiple of 256).
-// Returns KATS_OK with *done = false when the tensor-core path cannot run
-// (no tensor-map encoder, misaligned buffers), leaving the caller to fall back.
-int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done)
+// C[M][ldc] = A[M][K] . B on the tensor cores, B as hi / lo [N][K] (3xTF32).  Returns KATS_OK
+// with *done = false when the tensor-core path cannot run (no tensor-map encoder, misaligned
+// buffers or sizes), leaving the caller to fall back.
+int launch_hilbert_tc_op(const Plan &p, const float *A, int64_t M, int64_t K, const float *b_hi, const float *b_lo,
+                         int64_t N, float *C, int ldc, cudaStream_t st, bool *done)
 {
     *done = false;
     EncodeFn enc = encoder();
-    if (!enc || M < 1 || ldc % TP_N != 0 || p.tc_n % TP_N != 0 || (reinterpret_cast<uintptr_t>(g3) % 16) != 0 ||
-        (reinterpret_cast<uintptr_t>(g4) % 16) != 0)
+    if (!enc || M < 1 || K % TC_K != 0 || N % TP_N != 0 || ldc % TP_N != 0 || ldc < N ||
+        (reinterpret_cast<uintptr_t>(A) % 16) != 0 || (reinterpret_cast<uintptr_t>(C) % 16) != 0)
         return KATS_OK;
     CUtensorMap mA, mBh, mBl;
-    if (!encode_2d(enc, &mA, g3, p.tc_k, M, TC_K, TC_M) || !encode_2d(enc, &mBh, p.bt_hi, p.tc_k, p.tc_n, TC_K, TP_N) ||
-        !encode_2d(enc, &mBl, p.bt_lo, p.tc_k, p.tc_n, TC_K, TP_N))
+    if (!encode_2d(enc, &mA, A, K, M, TC_K, TC_M) || !encode_2d(enc, &mBh, b_hi, K, N, TC_K, TP_N) ||
+        !encode_2d(enc, &mBl, b_lo, K, N, TC_K, TP_N))
         return KATS_OK;
-    TcArgs a{g4, M, ldc, (int)(p.tc_k / TC_K), p.dev_status};
+    TcArgs a{C, M, ldc, (int)(K / TC_K), p.dev_status};
     using SH = TpShape<TP_N, TP_STAGES>;
     auto kern = k_hilbert_tc<TP_N, TP_STAGES>;
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM));
     int dev = 0, sms = 0;
     KATS_CUDA(cudaGetDevice(&dev));
     KATS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int n_ntiles = (int)(p.tc_n / TP_N);
+    const int n_ntiles = (int)(N / TP_N);
     const int64_t n_tiles = (int64_t)n_ntiles * ceil_div(M, TC_M);
     kern<<<(unsigned)std::min<int64_t>(sms, n_tiles), TP_THREADS, SH::SMEM, st>>>(mA, mBh, mBl, a, n_ntiles, n_tiles);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *done = true;
     return KATS_OK;
+}
+
+// g4[M][ldc] = g3[M][tc_k] . T on the tensor cores (ldc a multiple of 256).
+int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done)
+{
+    return launch_hilbert_tc_op(p, g3, M, p.tc_k, p.bt_hi, p.bt_lo, p.tc_n, g4, ldc, st, done);
 }
 
 }  // namespace kats

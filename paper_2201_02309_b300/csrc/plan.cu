@@ -534,7 +534,7 @@ static void free_plan(Plan *p)
     if (!p) return;
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
                     p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status,
-                    p->bt_hi, p->bt_lo, p->trig_lo, p->bt16_hi[0], p->bt16_lo[0], p->bt16_hi[1],
+                    p->bt_hi, p->bt_lo, p->btT_hi, p->btT_lo, p->trig_lo, p->bt16_hi[0], p->bt16_lo[0], p->bt16_hi[1],
                     p->bt16_lo[1]};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -568,6 +568,7 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->trig, g.views_per_turn)) || (rc = dalloc(p, &p->trig_lo, g.views_per_turn)) ||
         (rc = dalloc(p, &p->dev_status, 1)) ||
         (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)) ||
+        (rc = dalloc(p, &p->btT_hi, p->tct_n * p->tct_k)) || (rc = dalloc(p, &p->btT_lo, p->tct_n * p->tct_k)) ||
         (rc = dalloc(p, &p->bt16_hi[0], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[0], p->tc_n * p->tc_k16)) ||
         (rc = dalloc(p, &p->bt16_hi[1], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[1], p->tc_n * p->tc_k16)))
         return rc;
@@ -625,6 +626,15 @@ static int build(Plan *p)
             }
         KATS_CUDA(cudaMemcpyAsync(p->bt_hi, bhi.data(), bhi.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         KATS_CUDA(cudaMemcpyAsync(p->bt_lo, blo.data(), blo.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        // the transpose's operand, the same values with the roles of c and c' swapped
+        std::vector<float> thi((size_t)(p->tct_n * p->tct_k), 0.0f), tlo((size_t)(p->tct_n * p->tct_k), 0.0f);
+        for (int64_t cp = 0; cp < p->nc1; ++cp)
+            for (int64_t c = 0; c < nc; ++c) {
+                thi[(size_t)(cp * p->tct_k + c)] = bhi[(size_t)(c * p->tc_k + cp)];
+                tlo[(size_t)(cp * p->tct_k + c)] = blo[(size_t)(c * p->tc_k + cp)];
+            }
+        KATS_CUDA(cudaMemcpyAsync(p->btT_hi, thi.data(), thi.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        KATS_CUDA(cudaMemcpyAsync(p->btT_lo, tlo.data(), tlo.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         // 16-bit pairs: hi = value rounded to the type, lo = remainder rounded to the type
         const size_t n16 = (size_t)(p->tc_n * p->tc_k16);
         std::vector<uint16_t> h16(n16, 0), l16(n16, 0);
@@ -803,6 +813,8 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->gf_cols = (g->n_cols + 3) / 4 * 4;
     p->tc_k = (p->nc1 + 31) / 32 * 32;
     p->tc_n = (g->n_cols + 255) / 256 * 256;
+    p->tct_k = (g->n_cols + 31) / 32 * 32;
+    p->tct_n = (p->nc1 + 255) / 256 * 256;
     p->tc_k16 = (p->nc1 + 63) / 64 * 64;
     rc = build(p);
     if (rc) {
