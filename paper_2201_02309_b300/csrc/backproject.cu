@@ -972,6 +972,8 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
     extern __shared__ int win[];  // [2 windows][2 planes][slot_floats] fixed-point sums
     __shared__ int s_col[3];
+    // staged rows [s_rlo, s_rhi] touched in view j, slot j % 3 (reset two views ahead of its use)
+    __shared__ int s_rlo[3], s_rhi[3];
     __shared__ int s_K0, s_K1;
     __shared__ float s_fmax[BT_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1022,6 +1024,10 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     if (tid == 0) {
         s_K0 = INT32_MAX;
         s_K1 = INT32_MIN;
+        for (int q = 0; q < 3; ++q) {
+            s_rlo[q] = INT32_MAX;
+            s_rhi[q] = -1;
+        }
     }
     float fm = 0.0f;
 #pragma unroll
@@ -1079,8 +1085,15 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
         const int b = j & 1;
         if (warp == 0 && j + 1 < nviews) {
             const int c = window_col(k + 1);
-            if (lane == 0) s_col[(j + 1) % 3] = c;
+            if (lane == 0) {
+                s_col[(j + 1) % 3] = c;
+                // the band of view j + 1 is filled after this iteration's barrier; its slot was last
+                // read by the drain of view j - 2, which every thread finished before view j - 1's barrier
+                s_rlo[(j + 1) % 3] = INT32_MAX;
+                s_rhi[(j + 1) % 3] = -1;
+            }
         }
+        int r_first = INT32_MAX, r_last = -1;  // staged rows this thread deposits into in view k
         if (active && k >= kmin && k <= kmax) {
             const float2 cs = __ldg(a.trig + km);
             const float v = fmaf(-x, cs.x, fmaf(-y, cs.y, a.R));
@@ -1102,6 +1115,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
             // qa + PITCH pending) and deposit a row once the run has moved past it.
             constexpr uint32_t kNone = 0xFFFFFFFFu;
             uint32_t qa = kNone;  // window offset of the pending top row
+            uint32_t q_first = kNone;
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;  // pending rows, columns ci and ci + 1
 #pragma unroll
             for (int t = 0; t < B2_T; ++t) {
@@ -1121,6 +1135,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 const float fr = ur - (yv - 8388608.0f);
                 const float top = wv * scale * (1.0f - fr), bot = wv * scale * fr;
                 if (q != qa) {
+                    if (qa == kNone) q_first = q;
                     if (qa != kNone) {
                         deposit(win + qa, slot_floats, a0);
                         deposit(win + qa + 1, slot_floats, a1);
@@ -1148,7 +1163,16 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 deposit(win + qa + 1, slot_floats, a1);
                 deposit(win + qa + PITCH, slot_floats, b0);
                 deposit(win + qa + PITCH + 1, slot_floats, b1);
+                const uint32_t base = colx + (0x4B000000u << SH);  // window offset of staged row 0
+                r_first = (int)((q_first - base) >> SH);
+                r_last = (int)((qa - base) >> SH) + 1;
             }
+        }
+        r_first = __reduce_min_sync(0xffffffffu, r_first);
+        r_last = __reduce_max_sync(0xffffffffu, r_last);
+        if (lane == 0 && r_last >= 0) {
+            atomicMin(&s_rlo[j % 3], r_first);
+            atomicMax(&s_rhi[j % 3], r_last);
         }
         if (++km == a.vpt) km = 0;
         __syncthreads();  // window b of view k is complete; window b^1 (view k-1) has been drained
@@ -1156,7 +1180,10 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
         const int col0 = s_col[j % 3];
         int *w = win + 2 * b * slot_floats;
         float *view = gF + (int64_t)(k - a.first_view) * per_view;
-        for (int e = tid; e < wsize; e += BT_THREADS) {
+        // only the staged rows some thread deposited into can be nonzero
+        const int rlo = s_rlo[j % 3], rhi = s_rhi[j % 3];
+        const int e_end = rhi >= 0 ? min((rhi + 1) * PITCH, wsize) : 0;
+        for (int e = (rhi >= 0 ? rlo * PITCH : 0) + tid; e < e_end; e += BT_THREADS) {
             const int hi = w[e], lo = w[e + slot_floats];
             if ((hi | lo) == 0) continue;
             w[e] = 0;
