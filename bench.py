@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32",
                     help="storage precision of the intermediate data (precision form)")
+    ap.add_argument("--shard", choices=["replicas", "slabs"], default="replicas",
+                    help="N > 1: one volume per rank (weak scaling) or one volume split into z-slabs (strong)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
@@ -256,24 +258,38 @@ def run_ours(args):
     plan = kats.Plan(g)
     info = plan.info
     prec = {"fp32": kats.KATS_PREC_FP32, "bf16": kats.KATS_PREC_BF16, "fp16": kats.KATS_PREC_FP16}[args.precision]
+    slabs = args.shard == "slabs"
     sino = torch.from_numpy(sino_np).to(dev)
     vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
     ws = plan.workspace(precision=prec, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if slabs:
+        # this rank's slices of the one volume and just the sinogram views they read
+        s0, s1 = kats.slab_partition(g["nz"], world)[rank]
+        vb, vc = plan.slab_views(s0, s1) if s1 > s0 else (0, 0)
+        win = sino[vb:vb + vc].clone()
+        vol_slab = torch.empty((s1 - s0, g["ny"], g["nx"]), dtype=torch.float32, device=dev)
+        del sino
+
+    def step():
+        if not slabs:
+            plan.recon(sino, out=vol, workspace=ws, precision=prec)
+        elif s1 > s0:
+            plan.recon_slab(win, vb, s0, s1, out=vol_slab, workspace=ws, precision=prec)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
+    def max_over_ranks(x, op=None):
         if world == 1:
             return x
         t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=op or dist.ReduceOp.MAX)
         return float(t.item())
 
     for _ in range(args.warmup):
-        plan.recon(sino, out=vol, workspace=ws, precision=prec)
+        step()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -283,18 +299,19 @@ def run_ours(args):
     n_launch0 = kats.native.katsevich_launch_count()
     e0.record(stream)
     for _ in range(args.steps):
-        plan.recon(sino, out=vol, workspace=ws, precision=prec)
+        step()
     e1.record(stream)
     launches = kats.native.katsevich_launch_count() - n_launch0  # the library's own count
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms, value = job_throughput(e0.elapsed_time(e1) / args.steps, info["update_count"], world, max_over_ranks)
-    updates = info["update_count"] * world
+    volumes = 1 if slabs else world  # volumes the whole job reconstructs per step
+    ms, value = job_throughput(e0.elapsed_time(e1) / args.steps, info["update_count"], volumes, max_over_ranks)
+    updates = info["update_count"] * volumes
 
     roofline = None
-    if args.precision == "fp32":
+    if args.precision == "fp32" and not slabs:
         # per-kernel durations over the same work (events on the launching stream)
         gF = torch.empty(plan.filtered_shape, dtype=torch.float32, device=dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
@@ -335,7 +352,31 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and slabs:
+        # the slab's views from pinned host memory, the slab back: sequential copies around recon_slab
+        hs = torch.from_numpy(sino_np[vb:vb + vc]).pin_memory()
+        hv = torch.empty(tuple(vol_slab.shape), dtype=torch.float32).pin_memory()
+
+        def host_step():
+            win.copy_(hs, non_blocking=True)
+            step()
+            hv.copy_(vol_slab, non_blocking=True)
+            torch.cuda.synchronize()
+        for _ in range(max(1, args.warmup)):
+            host_step()
+        barrier()
+        times = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            host_step()
+            times.append(time.perf_counter() - t)
+        te = max_over_ranks(statistics.mean(times))
+        # bytes of the whole job: every rank's copies
+        h2d = max_over_ranks(float(hs.numel() * 4), dist.ReduceOp.SUM)
+        d2h = max_over_ranks(float(hv.numel() * 4), dist.ReduceOp.SUM)
+        e2e = {"value": updates / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": te * 1e3}
+    elif not args.no_e2e:
         hs = torch.from_numpy(sino_np).pin_memory()
         hv = torch.empty(plan.vol_shape, dtype=torch.float32).pin_memory()
         wsh = torch.empty(kats.native.katsevich_host_workspace_bytes(plan.handle, 1, prec), dtype=torch.uint8,
@@ -354,15 +395,18 @@ def run_ours(args):
                "d2h_bytes_per_step": int(np.prod(plan.vol_shape)) * 4, "ms_per_step": te * 1e3}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not slabs:
         cpu = oracle_sample(g, sino_np, info)
         cpu.pop("seconds", None)
 
     if rank == 0:
+        config = describe(cfg, g, info, args.precision)
+        config["parallelism"] = f"z-slabs x{world}" if slabs else f"replicas x{world}"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong" if slabs else "weak",
                 "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
-                "data": "synthetic", "config": describe(cfg, g, info, args.precision), "vol_per_s": world / (ms / 1e3),
+                "data": "synthetic", "config": config, "vol_per_s": volumes / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)

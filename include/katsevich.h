@@ -221,6 +221,35 @@ KATS_API int katsevich_recon_host(const kats_plan *plan, const float *host_sino,
                          int precision, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * z-slab partition of one reconstruction (Sec. II backprojection step: a voxel
+ * takes only the views of its PI interval, so a range of slices needs only the
+ * views whose half-view lies in the union of its voxels' PI windows; the paper
+ * backprojects slice by slice for the same reason).  Host only.
+ * katsevich_slab_views: the sinogram views [*view_begin, *view_begin +
+ * *view_count) that slices [s_begin, s_end) of the plan's volume read
+ * (0 <= s_begin < s_end <= nz; *view_count is 0 when no voxel of the range has
+ * a PI window).  Neighbouring slabs overlap in views (the PI windows are longer
+ * than one turn's share), not in slices.
+ */
+KATS_API int katsevich_slab_views(const kats_plan *plan, int64_t s_begin, int64_t s_end, int64_t *view_begin,
+                                  int64_t *view_count);
+
+/*
+ * Steps 1-7 for slices [s_begin, s_end) of one volume, from just the views the
+ * slab reads: sino_views [view_count][n_rows][n_cols] (device) holds sinogram
+ * views [view_begin, view_begin + view_count), which must cover the range
+ * katsevich_slab_views returns; vol_slab [s_end - s_begin][ny][nx] (device)
+ * receives the slab.  s_begin must be a multiple of 16 (the backprojection's
+ * slice tile): the slab then equals slices [s_begin, s_end) of katsevich_recon
+ * bit for bit, in every precision.  `workspace` as for katsevich_recon.  One
+ * slab per GPU, with no exchange between them, is the multi-GPU partition of a
+ * single volume.  Stream-ordered and asynchronous.
+ */
+KATS_API int katsevich_recon_slab(const kats_plan *plan, const float *sino_views, int64_t view_begin,
+                                  int64_t view_count, int64_t s_begin, int64_t s_end, float *vol_slab, int precision,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Copy a plan table to host memory (for checks against an independent
  * implementation).  which: 0 kappa row index (int32 [n_psi][n_cols-1]),
  * 1 kappa weight (float), 2 psi index (int32 [n_rows][n_cols]), 3 psi weight

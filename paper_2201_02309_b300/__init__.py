@@ -17,7 +17,7 @@ from . import native
 from .native import (KATS_ENDPOINT_FRACTIONAL, KATS_ENDPOINT_HARD, KATS_PREC_BF16, KATS_PREC_FP16,  # noqa: F401
                      KATS_PREC_FP32, KatsevichError)
 
-__all__ = ["Plan", "make_geometry", "KatsevichError", "native"]
+__all__ = ["Plan", "make_geometry", "slab_partition", "KatsevichError", "native"]
 
 
 def make_geometry(cfg: dict) -> dict:
@@ -184,6 +184,32 @@ class Plan:
                                     workspace.data_ptr(), n, _stream_ptr(stream))
         return host_vol
 
+    # -- z-slab partition (one volume over several GPUs: one slab each, no exchange)
+    def slab_views(self, s_begin: int, s_end: int):
+        """(view_begin, view_count): the sinogram views slices [s_begin, s_end) read."""
+        return native.katsevich_slab_views(self.handle, s_begin, s_end)
+
+    def recon_slab(self, sino_views, view_begin: int, s_begin: int, s_end: int, out=None,
+                   precision=KATS_PREC_FP32, stream=None, workspace=None):
+        """Slices [s_begin, s_end) (s_begin a multiple of 16) from sinogram views
+        [view_begin, view_begin + len(sino_views)); equal bit for bit to those slices of recon()."""
+        torch = _torch()
+        g = self.geom
+        if sino_views.dtype != torch.float32 or not sino_views.is_cuda or not sino_views.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        if sino_views.dim() != 3 or tuple(sino_views.shape[1:]) != (g["n_rows"], g["n_cols"]):
+            raise ValueError(f"expected [views][{g['n_rows']}][{g['n_cols']}], got {tuple(sino_views.shape)}")
+        shape = (s_end - s_begin, g["ny"], g["nx"])
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=sino_views.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 output of shape {shape}")
+        ws = workspace if workspace is not None else self.workspace(precision, sino_views.device)
+        native.katsevich_recon_slab(self.handle, sino_views.data_ptr(), view_begin, sino_views.shape[0], s_begin,
+                                    s_end, out.data_ptr(), precision, ws.data_ptr(), ws.numel() * ws.element_size(),
+                                    _stream_ptr(stream))
+        return out
+
     # -- tables (for checks)
     def table(self, name: str) -> np.ndarray:
         which, dt, kind = self.TABLES[name]
@@ -197,6 +223,22 @@ class Plan:
         a = np.empty(shape, dt)
         native.katsevich_plan_table(self.handle, which, a.ctypes.data, a.nbytes)
         return a
+
+
+def slab_partition(nz: int, world: int, tile: int = 16):
+    """Contiguous slice ranges [(s_begin, s_end)] for `world` ranks: every start a
+    multiple of `tile` (the backprojection's slice tile), tile counts as even as
+    possible, earlier ranks taking the extra tiles; a rank left without a tile gets
+    an empty range (s, s)."""
+    if nz < 1 or world < 1 or tile < 1:
+        raise ValueError("nz, world and tile must be >= 1")
+    n_tiles = -(-nz // tile)
+    out, t0 = [], 0
+    for r in range(world):
+        t1 = t0 + n_tiles // world + (1 if r < n_tiles % world else 0)
+        out.append((min(t0 * tile, nz), min(t1 * tile, nz)))
+        t0 = t1
+    return out
 
 
 def pi_endpoints(geom: dict, xyz: np.ndarray):

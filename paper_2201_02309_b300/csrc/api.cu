@@ -354,6 +354,75 @@ int katsevich_filter_adjoint(const kats_plan *plan, const float *gF, float *sino
     return KATS_OK;
 }
 
+int katsevich_slab_views(const kats_plan *plan, int64_t s_begin, int64_t s_end, int64_t *view_begin,
+                         int64_t *view_count)
+{
+    if (!plan || !view_begin || !view_count) {
+        set_error("null plan or output");
+        return KATS_EINVAL;
+    }
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    if (s_begin < 0 || s_end <= s_begin || s_end > p.g.nz) {
+        set_error("slices [%lld, %lld) not a non-empty range of [0, %lld)", (long long)s_begin, (long long)s_end,
+                  (long long)p.g.nz);
+        return KATS_EINVAL;
+    }
+    int64_t lo, hi;
+    slab_views(p, s_begin, s_end, &lo, &hi);
+    // filtered half-views [lo, hi] (relative to first_view) are formed from sinogram views [lo, hi + 1]
+    *view_begin = hi >= lo ? p.first_view + lo : p.first_view;
+    *view_count = hi >= lo ? hi - lo + 2 : 0;
+    return KATS_OK;
+}
+
+int katsevich_recon_slab(const kats_plan *plan, const float *sino_views, int64_t view_begin, int64_t view_count,
+                         int64_t s_begin, int64_t s_end, float *vol_slab, int precision, void *workspace,
+                         size_t workspace_bytes, void *stream)
+{
+    kats::NvtxRange nvtx_range("katsevich: recon slab");
+    int rc = check_common(plan, sino_views, vol_slab, 1, precision, workspace, true);
+    if (rc) return rc;
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    int64_t need_begin = 0, need_count = 0;
+    rc = katsevich_slab_views(plan, s_begin, s_end, &need_begin, &need_count);
+    if (rc) return rc;
+    if (s_begin % 16 != 0) {
+        set_error("slab start %lld is not a multiple of 16 slices", (long long)s_begin);
+        return KATS_EINVAL;
+    }
+    if (need_count > 0 && (view_begin > need_begin || view_begin + view_count < need_begin + need_count)) {
+        set_error("sinogram views [%lld, %lld) do not cover the slab's views [%lld, %lld)", (long long)view_begin,
+                  (long long)(view_begin + view_count), (long long)need_begin, (long long)(need_begin + need_count));
+        return KATS_EINVAL;
+    }
+    const size_t need = recon_ws_for(p, precision);
+    if (workspace_bytes < need) {
+        set_error("workspace %zu < %zu bytes", workspace_bytes, need);
+        return KATS_ESPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp32 = precision == KATS_PREC_FP32;
+    const size_t gfb = fp32 ? align256(gf_bytes(p)) : align256(gfp_bytes(p));
+    char *fws = (char *)workspace + gfb;
+    const int64_t lo = need_begin - p.first_view, nv = std::max<int64_t>(need_count - 1, 0);
+    const float *first = sino_views + (need_begin - view_begin) * (int64_t)view_elems(p);
+    // the filtered views land at their places in the full-size g^F layout, so the backprojection
+    // indexes them as in katsevich_recon; its slice tiles start at s_begin, a multiple of 16 as in
+    // the full volume, so every slice is added in the same order and equals katsevich_recon's
+    if (nv > 0) {
+        rc = fp32 ? launch_filter(p, first, (float *)workspace + lo * p.g.n_rows * p.gf_cols, fws, need - gfb, st, nv)
+                  : launch_filter16(p, precision, first, (uint32_t *)workspace + lo * (p.g.n_rows + 1) * p.gf_cols,
+                                    fws, need - gfb, st, nv);
+        if (rc) return rc;
+    }
+    // vol_slab holds slices [s_begin, s_end); the kernels address slice s at base + s * nx * ny
+    float *base = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(vol_slab) -
+                                            sizeof(float) * (uintptr_t)(s_begin * p.g.nx * p.g.ny));
+    const int n = (int)(s_end - s_begin);
+    return fp32 ? launch_backproject(p, (const float *)workspace, base, st, (int)s_begin, n)
+                : launch_backproject16(p, precision, (const uint32_t *)workspace, base, st, (int)s_begin, n);
+}
+
 int64_t katsevich_host_workspace_bytes(const kats_plan *plan, int batch, int precision)
 {
     if (!plan || batch < 1 || (precision != KATS_PREC_FP32 && precision != KATS_PREC_BF16 &&

@@ -20,7 +20,8 @@ _STATUS = {1: "KATS_EINVAL", 2: "KATS_EGEOM", 3: "KATS_ENOMEM", 4: "KATS_ECUDA",
 # Every symbol include/katsevich.h declares.
 EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "katsevich_workspace_bytes",
            "katsevich_recon", "katsevich_adjoint", "katsevich_filter", "katsevich_backproject",
-           "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_plan_table",
+           "katsevich_host_workspace_bytes", "katsevich_recon_host", "katsevich_slab_views",
+           "katsevich_recon_slab", "katsevich_plan_table",
            "katsevich_pi_endpoints", "katsevich_plan_destroy", "katsevich_last_error",
            "katsevich_recon_noalloc", "katsevich_device_status", "katsevich_backproject_adjoint",
            "katsevich_filter_adjoint", "katsevich_server_create", "katsevich_server_submit",
@@ -107,6 +108,10 @@ def load() -> ctypes.CDLL:
         "katsevich_backproject": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_host_workspace_bytes": (ctypes.c_int64, [P, ctypes.c_int, ctypes.c_int]),
         "katsevich_recon_host": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "katsevich_slab_views": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64)]),
+        "katsevich_recon_slab": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                P, ctypes.c_int, P, ctypes.c_size_t, P]),
         "katsevich_plan_table": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_size_t]),
         "katsevich_pi_endpoints": (ctypes.c_int, [ctypes.POINTER(kats_geometry), ctypes.c_int64, P, P, P]),
         "katsevich_plan_destroy": (None, [P]),
@@ -225,6 +230,19 @@ def katsevich_host_workspace_bytes(plan, batch, precision=KATS_PREC_FP32) -> int
 def katsevich_recon_host(plan, host_sino_ptr, host_vol_ptr, batch, precision, ws_ptr, ws_bytes, stream_ptr) -> None:
     check(load().katsevich_recon_host(plan, host_sino_ptr, host_vol_ptr, batch, precision, ws_ptr, ws_bytes,
                                       stream_ptr))
+
+
+def katsevich_slab_views(plan, s_begin, s_end) -> tuple:
+    """(view_begin, view_count): the sinogram views slices [s_begin, s_end) read."""
+    vb, vc = ctypes.c_int64(), ctypes.c_int64()
+    check(load().katsevich_slab_views(plan, s_begin, s_end, ctypes.byref(vb), ctypes.byref(vc)))
+    return vb.value, vc.value
+
+
+def katsevich_recon_slab(plan, sino_ptr, view_begin, view_count, s_begin, s_end, vol_ptr, precision, ws_ptr,
+                         ws_bytes, stream_ptr) -> None:
+    check(load().katsevich_recon_slab(plan, sino_ptr, view_begin, view_count, s_begin, s_end, vol_ptr, precision,
+                                      ws_ptr, ws_bytes, stream_ptr))
 
 
 def katsevich_plan_table(plan, which, dst_ptr, nbytes) -> None:
