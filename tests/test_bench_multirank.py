@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_throughput_uses_slowest_rank():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_worker, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
         res = dict(out)

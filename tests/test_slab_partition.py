@@ -57,7 +57,7 @@ def _worker(rank, world, port, nz, out):
 def test_two_ranks_cover_the_volume_once():
     nz = 256
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_worker, args=(2, port, nz, out), nprocs=2, join=True, start_method="spawn")
         res = dict(out)
