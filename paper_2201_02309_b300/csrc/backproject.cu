@@ -196,8 +196,10 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 // ---------------------------------------------------------------- TMA kernel
 // CTA = B2_TX x B2_TY columns x B2_T slices: B2_CW consumer warps (one thread
 // per column) plus one producer warp that stages each view's detector window
-// into a ring of B2_R shared-memory slots (full/empty mbarrier pairs).
-constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16, B2_R = 5;
+// into a ring of B2_R shared-memory slots.  Consumers take two views per
+// iteration, so the slots go in pairs, each pair with one full / empty
+// mbarrier: one wait and one release per two views.
+constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16, B2_RP = 3, B2_R = 2 * B2_RP;
 constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
 constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
@@ -453,9 +455,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t s_full[B2_R], s_empty[B2_R];
-    __shared__ int s_col[B2_R];
-    __shared__ float2 s_cs[B2_R];
+    __shared__ __align__(8) uint64_t s_full[B2_RP], s_empty[B2_RP];
+    __shared__ int2 s_col[B2_RP];     // first window column of the pair's two views
+    __shared__ float4 s_cs[B2_RP];    // (cos, sin) of the pair's two views
     __shared__ int s_K0, s_K1;
     const BPArgs &a = p.a;
     const int tid = threadIdx.x;
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     if (tid == 0) {
         s_K0 = INT32_MAX;
         s_K1 = INT32_MIN;
-        for (int r = 0; r < B2_R; ++r) {
+        for (int r = 0; r < B2_RP; ++r) {
             mbar_init(&s_full[r], 1);
             mbar_init(&s_empty[r], B2_CW);
         }
@@ -551,43 +553,51 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
         const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
         const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
-        int slot = 0, issued = 0;
+        int ps = 0, issued = 0;  // pair slot; view pairs issued
         uint32_t phase = 0;
         int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
         bool ok = true;
-        for (int j = 0; j < nviews; ++j) {
-            if (j >= B2_R && !mbar_wait(&s_empty[slot], phase ^ 1u)) {
+        for (int j = 0; j < nviews; j += 2) {
+            if (j >= B2_R && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
                 ok = false;
                 break;
             }
-            const float2 cs = __ldg(a.trig + kmod);
-            const float v = a.R - cx * cs.x - cy * cs.y;
-            const float u = -cx * cs.y + cy * cs.x;
-            float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
-            c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
-            c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
-            if (lane == 0) {
+            const int nv2 = min(2, nviews - j);
+            const int kmod1 = kmod + 1 == a.vpt ? 0 : kmod + 1;
+            const float2 csA = __ldg(a.trig + kmod), csB = __ldg(a.trig + kmod1);
+            int clo[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 cs = h ? csB : csA;
+                const float v = a.R - cx * cs.x - cy * cs.y;
+                const float u = -cx * cs.y + cy * cs.x;
+                float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
+                c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
+                c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
                 // one column of slack left of the lowest tap, start aligned to 4 floats (16 bytes)
-                const int clo = ((int)floorf(c) - 1) & ~3;
-                s_col[slot] = clo;
-                s_cs[slot] = cs;
-                mbar_arrive_expect_tx(&s_full[slot], box_bytes);
+                clo[h] = ((int)floorf(c) - 1) & ~3;
+            }
+            if (lane == 0) {
+                s_col[ps] = make_int2(clo[0], clo[1]);
+                s_cs[ps] = make_float4(csA.x, csA.y, csB.x, csB.y);
+                mbar_arrive_expect_tx(&s_full[ps], box_bytes * (uint32_t)nv2);
                 // fp32 windows start one zero row above the detector; row-pair windows at pair-row 0
-                tma_load_3d(dst0 + 4u * (uint32_t)(slot * p.slot_floats), &gmap, &s_full[slot], clo, MODE == 0 ? -1 : 0,
-                            K0 + j - (int)a.first_view);
+                for (int h = 0; h < nv2; ++h)
+                    tma_load_3d(dst0 + 4u * (uint32_t)((2 * ps + h) * p.slot_floats), &gmap, &s_full[ps], clo[h],
+                                MODE == 0 ? -1 : 0, K0 + j + h - (int)a.first_view);
             }
             __syncwarp();
-            issued = j + 1;
-            if (++slot == B2_R) {
-                slot = 0;
+            issued = j / 2 + 1;
+            if (++ps == B2_RP) {
+                ps = 0;
                 phase ^= 1u;
             }
-            if (++kmod == a.vpt) kmod = 0;
+            kmod = kmod1 + 1 == a.vpt ? 0 : kmod1 + 1;
         }
         if (!ok && lane == 0) {
             // let every issued copy land before the CTA's shared memory is released
-            for (int j = max(0, issued - B2_R); j < issued; ++j)
-                mbar_wait(&s_full[j % B2_R], (uint32_t)((j / B2_R) & 1));
+            for (int i = max(0, issued - B2_RP); i < issued; ++i)
+                mbar_wait(&s_full[i % B2_RP], (uint32_t)((i / B2_RP) & 1));
             atomicExch(p.status, kDevStatusTimeout);
         }
         return;
@@ -601,14 +611,12 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     z_base(a, s0, kbase, &zb, &zb_lo);
     const float rmax = (float)(a.n_rows + 1);
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-    int slot = 0;
+    int ps = 0;  // pair slot: views kA and kB in slots 2 ps and 2 ps + 1
     uint32_t phase = 0;
     for (int j = 0; j < nviews; j += 2) {
         const int kA = K0 + j, kB = kA + 1;
         const bool hasB = j + 1 < nviews;
-        const int slotB = slot + 1 == B2_R ? 0 : slot + 1;
-        const uint32_t phaseB = slot + 1 == B2_R ? phase ^ 1u : phase;
-        if (!mbar_wait(&s_full[slot], phase) || (hasB && !mbar_wait(&s_full[slotB], phaseB))) {
+        if (!mbar_wait(&s_full[ps], phase)) {
             if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
             return;  // the producer's own bounded waits end the CTA
         }
@@ -617,16 +625,18 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         if (onA || onB) {
             const float kfA = (float)(kA - kbase);
             ViewGeo2 g;
-            view_geo2<POLY>(a, x, y, s_cs[slot], s_cs[slotB], zb, zb_lo, kfA, g);
+            const float4 cs4 = s_cs[ps];
+            const int2 col2 = s_col[ps];
+            view_geo2<POLY>(a, x, y, make_float2(cs4.x, cs4.y), make_float2(cs4.z, cs4.w), zb, zb_lo, kfA, g);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!(h ? onB : onA)) continue;
-                const int k = kA + h, sl = h ? slotB : slot;
+                const int k = kA + h, sl = 2 * ps + h, col0 = h ? col2.y : col2.x;
                 const float fc = h ? g.fc.y : g.fc.x, ur0 = h ? g.ur0.y : g.ur0.x, dur = h ? g.dur.y : g.dur.x;
                 const float inv_v = h ? g.inv_v.y : g.inv_v.x, kf = kfA + (float)h;
-                KATS_DCHECK((h ? g.ci1 : g.ci0) - s_col[sl] >= 0 && (h ? g.ci1 : g.ci0) - s_col[sl] <= p.W - 2, 1);
+                KATS_DCHECK((h ? g.ci1 : g.ci0) - col0 >= 0 && (h ? g.ci1 : g.ci0) - col0 <= p.W - 2, 1);
                 const uint32_t colx =
-                    (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - s_col[sl], 0), p.W - 2)) -
+                    (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - col0, 0), p.W - 2)) -
                     (0x4B000000u << SH);
                 // full: every slice inside its window with weight 1; ramps: windows
                 // still opening (no slice ended) or closing (every slice started)
@@ -642,14 +652,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             }
         }
         __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(&s_empty[slot]);
-            if (hasB) mbar_arrive(&s_empty[slotB]);
-        }
-        slot = slotB;
-        phase = phaseB;
-        if (++slot == B2_R) {
-            slot = 0;
+        if (lane == 0) mbar_arrive(&s_empty[ps]);
+        if (++ps == B2_RP) {
+            ps = 0;
             phase ^= 1u;
         }
     }
