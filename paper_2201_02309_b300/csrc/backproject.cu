@@ -196,10 +196,11 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 // ---------------------------------------------------------------- TMA kernel
 // CTA = B2_TX x B2_TY columns x B2_T slices: B2_CW consumer warps (one thread
 // per column) plus one producer warp that stages each view's detector window
-// into a ring of B2_R shared-memory slots.  Consumers take two views per
+// into a ring of shared-memory slots.  Consumers take two views per
 // iteration, so the slots go in pairs, each pair with one full / empty
-// mbarrier: one wait and one release per two views.
-constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16, B2_RP = 3, B2_R = 2 * B2_RP;
+// mbarrier: one wait and one release per two views.  The ring holds RP
+// pairs, 3 or 2 (chosen at launch from the slot size).
+constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16;
 constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
 constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
@@ -450,14 +451,14 @@ __device__ __forceinline__ void view_geo2(const BPArgs &a, float x, float y, flo
 
 // RANGED: the launch takes a share of the views (BPArgs k_lo .. acc_final); the plain form
 // compiles without that bookkeeping.
-template <int PITCH, int MODE, bool POLY, bool ROWS_OK, bool RANGED>
+template <int PITCH, int MODE, bool POLY, bool ROWS_OK, bool RANGED, int RP>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t s_full[B2_RP], s_empty[B2_RP];
-    __shared__ int2 s_col[B2_RP];     // first window column of the pair's two views
-    __shared__ float4 s_cs[B2_RP];    // (cos, sin) of the pair's two views
+    __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
+    __shared__ int2 s_col[RP];     // first window column of the pair's two views
+    __shared__ float4 s_cs[RP];    // (cos, sin) of the pair's two views
     __shared__ int s_K0, s_K1;
     const BPArgs &a = p.a;
     const int tid = threadIdx.x;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     if (tid == 0) {
         s_K0 = INT32_MAX;
         s_K1 = INT32_MIN;
-        for (int r = 0; r < B2_RP; ++r) {
+        for (int r = 0; r < RP; ++r) {
             mbar_init(&s_full[r], 1);
             mbar_init(&s_empty[r], B2_CW);
         }
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
         bool ok = true;
         for (int j = 0; j < nviews; j += 2) {
-            if (j >= B2_R && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
+            if (j >= 2 * RP && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
                 ok = false;
                 break;
             }
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             }
             __syncwarp();
             issued = j / 2 + 1;
-            if (++ps == B2_RP) {
+            if (++ps == RP) {
                 ps = 0;
                 phase ^= 1u;
             }
@@ -596,8 +597,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         }
         if (!ok && lane == 0) {
             // let every issued copy land before the CTA's shared memory is released
-            for (int i = max(0, issued - B2_RP); i < issued; ++i)
-                mbar_wait(&s_full[i % B2_RP], (uint32_t)((i / B2_RP) & 1));
+            for (int i = max(0, issued - RP); i < issued; ++i)
+                mbar_wait(&s_full[i % RP], (uint32_t)((i / RP) & 1));
             atomicExch(p.status, kDevStatusTimeout);
         }
         return;
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[ps]);
-        if (++ps == B2_RP) {
+        if (++ps == RP) {
             ps = 0;
             phase ^= 1u;
         }
@@ -759,6 +760,19 @@ static int window_cols(const Plan &p)
     return ((int)ceil(span) + 8 + 3) / 4 * 4;
 }
 
+template <int PITCH, int MODE, int RP>
+static auto select_tma(bool ranged, bool poly, bool rows_ok)
+{
+    return ranged ? (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, true, RP>
+                                     : k_backproject_tma<PITCH, MODE, true, false, true, RP>)
+                          : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, true, RP>
+                                     : k_backproject_tma<PITCH, MODE, false, false, true, RP>))
+                  : (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, false, RP>
+                                     : k_backproject_tma<PITCH, MODE, true, false, false, RP>)
+                          : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, false, RP>
+                                     : k_backproject_tma<PITCH, MODE, false, false, false, RP>));
+}
+
 template <int PITCH, int MODE>
 static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched)
 {
@@ -766,9 +780,14 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     // staged rows: fp32 -> detector rows -1 .. n_rows + 1; row pairs -> pair-rows 0 .. n_rows + 1
     const int srows = (int)p.g.n_rows + (MODE == 0 ? 3 : 2);
     const int slot = (PITCH * srows + 31) / 32 * 32;
-    const size_t smem = sizeof(float) * (size_t)slot * B2_R + 128;  // + base alignment slack
+    // 3 slot pairs where two CTAs still fit on an SM (228 KB less 1 KB per CTA and the static shared
+    // memory), else 2 pairs; + 128 bytes of base alignment slack
+    auto ring_bytes = [&](int rp) { return sizeof(float) * (size_t)slot * 2 * rp + 128; };
+    constexpr size_t kTwoPerSm = 112 * 1024, kMax = 200 * 1024;
+    const int rp = ring_bytes(3) <= kTwoPerSm || ring_bytes(2) > kTwoPerSm ? (ring_bytes(3) <= kMax ? 3 : 2) : 2;
+    const size_t smem = ring_bytes(rp);
     EncodeTiledFn enc = encode_fn();
-    if (!enc || W > PITCH || PITCH > p.gf_cols || srows > 256 || smem > 200 * 1024 ||
+    if (!enc || W > PITCH || PITCH > p.gf_cols || srows > 256 || smem > kMax ||
         (reinterpret_cast<uintptr_t>(gF) % 16) != 0 || p.n_fviews >= INT32_MAX)
         return KATS_OK;
     const int64_t drows = p.g.n_rows + (MODE == 0 ? 0 : 1);
@@ -790,14 +809,8 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
     const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
     const bool ranged = a.k_lo != INT32_MIN || a.k_hi != INT32_MAX || a.acc_in || !a.acc_final;
-    auto kern = ranged ? (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, true>
-                                          : k_backproject_tma<PITCH, MODE, true, false, true>)
-                               : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, true>
-                                          : k_backproject_tma<PITCH, MODE, false, false, true>))
-                       : (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, false>
-                                          : k_backproject_tma<PITCH, MODE, true, false, false>)
-                               : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, false>
-                                          : k_backproject_tma<PITCH, MODE, false, false, false>));
+    auto kern = rp == 3 ? select_tma<PITCH, MODE, 3>(ranged, poly, rows_ok)
+                        : select_tma<PITCH, MODE, 2>(ranged, poly, rows_ok);
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
               (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));

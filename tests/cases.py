@@ -74,6 +74,18 @@ def c3_small_case():
     return cfg, g
 
 
+def rows80_case():
+    """The config-1 scanner with 80 detector rows: a staged view window of 64 columns x 83 rows
+    (21 KB) is too large for six ring slots at two CTAs per SM, so the backprojection runs with
+    four slots (two slot pairs)."""
+    cfg = dict(synth.config(1))
+    cfg.update(n_rows=80)
+    g = oracle.derive_geometry(cfg)
+    ell = synth.phantom_for(cfg, g, 81)
+    sino = synth.project(g, ell)
+    return cfg, g, sino.astype(np.float32)
+
+
 def tall_case():
     """A detector of 264 rows and 33 columns: 528 kappa lines and 264 rows are more
     table entries than the rebinning kernels keep in shared memory, and more rows
