@@ -132,11 +132,12 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     // slabs of whole 16-slice z tiles.  The first four are small: the first starts backprojecting
     // after a few chunks, and each further 16 slices need only about a chunk more of views, which
     // arrive faster than a small slab is backprojected, so the GPU is not left waiting for the
-    // copies; the middle slabs are 64 slices, the last small again (little to copy back at the end)
+    // copies; the middle slabs are up to 128 slices (fewer partly filled last waves), the last small
+    // again (little to copy back at the end)
     std::vector<int> slab_lo{0};
     while (slab_lo.back() < nz) {
         const int64_t s0 = slab_lo.back(), left = nz - s0;
-        const int64_t n = s0 < 64 ? 16 : (left <= 80 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 64);
+        const int64_t n = s0 < 64 ? 16 : (left <= 144 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 128);
         slab_lo.push_back((int)std::min<int64_t>(nz, s0 + std::max<int64_t>(n, 1)));
     }
     const int n_slabs = (int)slab_lo.size() - 1;
