@@ -56,26 +56,33 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
 
     debug=True also builds _lib/libkatsevich_debug.so: the same objects, except that the sources
     in DEBUG_SOURCES are compiled with KATS_DEBUG_CHECKS (kernel invariant checks); loaded when
-    KATSEVICH_DEBUG_CHECKS=1."""
+    KATSEVICH_DEBUG_CHECKS=1.  The nvcc calls run in parallel, one per source."""
+    from concurrent.futures import ThreadPoolExecutor
+
     os.makedirs(LIBDIR, exist_ok=True)
     objdir = os.path.join(HERE, "_build")
+    dbgdir = os.path.join(HERE, "_build_debug")
     os.makedirs(objdir, exist_ok=True)
     objs = [os.path.join(objdir, os.path.basename(src)[:-3] + ".o") for src in sources()]
-    if force or not up_to_date(LIB):
-        for src, obj in zip(sources(), objs):
-            _compile(src, obj, verbose)
+    rel = force or not up_to_date(LIB)
+    dbg = debug and (force or not up_to_date(LIB_DEBUG))
+    jobs = [(src, obj, ()) for src, obj in zip(sources(), objs)] if rel else []
+    dobjs = list(objs)
+    if dbg:
+        os.makedirs(dbgdir, exist_ok=True)
+        for i, src in enumerate(sources()):
+            if os.path.basename(src) in DEBUG_SOURCES:
+                dobjs[i] = os.path.join(dbgdir, os.path.basename(src)[:-3] + ".o")
+                jobs.append((src, dobjs[i], ("-DKATS_DEBUG_CHECKS",)))
+    if jobs:
+        with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as pool:
+            for f in [pool.submit(_compile, src, obj, verbose, list(defs)) for src, obj, defs in jobs]:
+                f.result()  # re-raises a failed compile
+    if rel:
         _link(LIB, objs)
     if not debug:
         return LIB
-    if force or not up_to_date(LIB_DEBUG):
-        dbgdir = os.path.join(HERE, "_build_debug")
-        os.makedirs(dbgdir, exist_ok=True)
-        dobjs = []
-        for src, obj in zip(sources(), objs):
-            if os.path.basename(src) in DEBUG_SOURCES:
-                obj = os.path.join(dbgdir, os.path.basename(src)[:-3] + ".o")
-                _compile(src, obj, verbose, ["-DKATS_DEBUG_CHECKS"])
-            dobjs.append(obj)
+    if dbg:
         _link(LIB_DEBUG, dobjs)
     return LIB_DEBUG
 
