@@ -91,6 +91,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// The same for K blocks of KB fp32 elements: rows of 4 KB bytes with a (4 KB)-byte swizzle
+// (layout type 2 = 128-byte, 4 = 64-byte), 8-row groups 8 x 4 KB bytes apart.
+template <int KB>
+__device__ __forceinline__ uint64_t swz_desc(uint32_t addr)
+{
+    static_assert(KB == 32 || KB == 16, "K block of 128 or 64 bytes");
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((8 * 4 * KB) >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)(KB == 32 ? 2 : 4) << 61);
+}
+
 template <uint32_t IDESC>
 __device__ __forceinline__ void mma_tf32_n(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
 {
@@ -145,26 +155,29 @@ struct TcArgs {
 // Every wait is bounded; on a timeout the CTA records a device status, lets its
 // issued MMAs finish and its copies land, and frees TMEM before returning.
 constexpr int TP_THREADS = 320;
-constexpr int TP_N = 256, TP_STAGES = 2;  // tile width and ring depth of the launched form
+// tile width, ring depth and K block of the launched form: 4 stages of K blocks of 16 (64-byte
+// rows) keep each stage's copies three stages ahead of the MMAs that read it
+constexpr int TP_N = 256, TP_STAGES = 4, TP_KB = 16;
 
-// Tile TC_M x N, STAGES-deep ring; one stage holds A, A_lo (TC_M x TC_K) and T_hi, T_lo (N x TC_K).
-template <int N, int STAGES>
+// Tile TC_M x N, STAGES-deep ring; one stage holds A, A_lo (TC_M x KB) and T_hi, T_lo (N x KB).
+template <int N, int STAGES, int KB>
 struct TpShape {
-    static constexpr uint32_t B_BYTES = N * TC_K * 4;
-    static constexpr uint32_t STAGE_BYTES = 2 * TC_A_BYTES + 2 * B_BYTES;
+    static constexpr uint32_t A_BYTES = TC_M * KB * 4;
+    static constexpr uint32_t B_BYTES = N * KB * 4;
+    static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
     // kind::tf32 instruction descriptor for TC_M x N
     static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
                                       ((uint32_t)(TC_M >> 4) << 24);
 };
 
-template <int N, int STAGES>
+template <int N, int STAGES, int KB>
 __global__ void __launch_bounds__(TP_THREADS, 1)
     k_hilbert_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
                    const __grid_constant__ CUtensorMap mapBl, TcArgs a, int n_ntiles, int64_t n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
-    using SH = TpShape<N, STAGES>;
+    using SH = TpShape<N, STAGES, KB>;
     __shared__ __align__(8) uint64_t s_full[STAGES], s_conv[STAGES], s_empty[STAGES];
     __shared__ __align__(8) uint64_t s_accf[2], s_acce[2], s_done;
     __shared__ uint32_t s_tmem;
@@ -174,9 +187,9 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
     const uint32_t base = (saddr(tc_raw) + 1023u) & ~1023u;  // 1024-byte aligned (128-byte swizzle atoms)
     unsigned char *const gbase = tc_raw + (base - saddr(tc_raw));
     auto stA = [&](int s) { return base + (uint32_t)s * SH::STAGE_BYTES; };
-    auto stAlo = [&](int s) { return stA(s) + TC_A_BYTES; };
-    auto stBh = [&](int s) { return stA(s) + 2 * TC_A_BYTES; };
-    auto stBl = [&](int s) { return stA(s) + 2 * TC_A_BYTES + SH::B_BYTES; };
+    auto stAlo = [&](int s) { return stA(s) + SH::A_BYTES; };
+    auto stBh = [&](int s) { return stA(s) + 2 * SH::A_BYTES; };
+    auto stBl = [&](int s) { return stA(s) + 2 * SH::A_BYTES + SH::B_BYTES; };
     const int nkb = a.kblocks;
     const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto tile_m0 = [&](int64_t i) { return ((int64_t)blockIdx.x + i * gridDim.x) / n_ntiles * TC_M; };
@@ -223,10 +236,10 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
                         break;
                     }
                     if (aborted()) break;
-                    bar_expect(&s_full[s], TC_A_BYTES + 2 * SH::B_BYTES);
-                    tma_2d(stA(s), &mapA, &s_full[s], kb * TC_K, (int)m0);
-                    tma_2d(stBh(s), &mapBh, &s_full[s], kb * TC_K, n0);
-                    tma_2d(stBl(s), &mapBl, &s_full[s], kb * TC_K, n0);
+                    bar_expect(&s_full[s], SH::A_BYTES + 2 * SH::B_BYTES);
+                    tma_2d(stA(s), &mapA, &s_full[s], kb * KB, (int)m0);
+                    tma_2d(stBh(s), &mapBh, &s_full[s], kb * KB, n0);
+                    tma_2d(stBl(s), &mapBl, &s_full[s], kb * KB, n0);
                     s_issued = g + 1;
                 }
             }
@@ -258,10 +271,10 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
                     }
                     fence_after();
 #pragma unroll
-                    for (int kk = 0; kk < TC_K / 8; ++kk) {  // 8 tf32 = 32 bytes per MMA
+                    for (int kk = 0; kk < KB / 8; ++kk) {  // 8 tf32 = 32 bytes per MMA
                         const uint32_t off = (uint32_t)kk * 32u;
-                        const uint64_t dA = sw128_desc(stA(s) + off), dAl = sw128_desc(stAlo(s) + off);
-                        const uint64_t dBh = sw128_desc(stBh(s) + off), dBl = sw128_desc(stBl(s) + off);
+                        const uint64_t dA = swz_desc<KB>(stA(s) + off), dAl = swz_desc<KB>(stAlo(s) + off);
+                        const uint64_t dBh = swz_desc<KB>(stBh(s) + off), dBl = swz_desc<KB>(stBl(s) + off);
                         mma_tf32_n<SH::IDESC>(acc, dA, dBh, (kb | kk) != 0);
                         mma_tf32_n<SH::IDESC>(acc, dA, dBl, 1u);
                         mma_tf32_n<SH::IDESC>(acc, dAl, dBh, 1u);
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
                 float4 *A = reinterpret_cast<float4 *>(gbase + (stA(s) - base));
                 float4 *L = reinterpret_cast<float4 *>(gbase + (stAlo(s) - base));
 #pragma unroll
-                for (int q = 0; q < (int)(TC_A_BYTES / 16) / 128; ++q) {
+                for (int q = 0; q < (int)(SH::A_BYTES / 16) / 128; ++q) {
                     const int e = ct + 128 * q;
                     float4 v = A[e], h, l;
                     h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -378,14 +391,14 @@ EncodeFn encoder()
 }
 
 bool encode_2d(EncodeFn enc, CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, int box_inner,
-               int box_outer)
+               int box_outer, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B)
 {
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -634,16 +647,17 @@ int launch_hilbert_tc_op(const Plan &p, const float *A, int64_t M, int64_t K, co
 {
     *done = false;
     EncodeFn enc = encoder();
-    if (!enc || M < 1 || K % TC_K != 0 || N % TP_N != 0 || ldc % TP_N != 0 || ldc < N ||
+    if (!enc || M < 1 || K % TP_KB != 0 || N % TP_N != 0 || ldc % TP_N != 0 || ldc < N ||
         (reinterpret_cast<uintptr_t>(A) % 16) != 0 || (reinterpret_cast<uintptr_t>(C) % 16) != 0)
         return KATS_OK;
     CUtensorMap mA, mBh, mBl;
-    if (!encode_2d(enc, &mA, A, K, M, TC_K, TC_M) || !encode_2d(enc, &mBh, b_hi, K, N, TC_K, TP_N) ||
-        !encode_2d(enc, &mBl, b_lo, K, N, TC_K, TP_N))
+    const CUtensorMapSwizzle swz = TP_KB == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    if (!encode_2d(enc, &mA, A, K, M, TP_KB, TC_M, swz) || !encode_2d(enc, &mBh, b_hi, K, N, TP_KB, TP_N, swz) ||
+        !encode_2d(enc, &mBl, b_lo, K, N, TP_KB, TP_N, swz))
         return KATS_OK;
-    TcArgs a{C, M, ldc, (int)(K / TC_K), p.dev_status};
-    using SH = TpShape<TP_N, TP_STAGES>;
-    auto kern = k_hilbert_tc<TP_N, TP_STAGES>;
+    TcArgs a{C, M, ldc, (int)(K / TP_KB), p.dev_status};
+    using SH = TpShape<TP_N, TP_STAGES, TP_KB>;
+    auto kern = k_hilbert_tc<TP_N, TP_STAGES, TP_KB>;
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM));
     int dev = 0, sms = 0;
     KATS_CUDA(cudaGetDevice(&dev));
