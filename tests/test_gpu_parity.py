@@ -212,6 +212,29 @@ def test_narrow_detector_fallback_path(kats, torch):
     assert rel_l2(got, op.adjoint(y.astype(np.float64))) < TOL
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 17, 3), (33, 1, 1), (17, 18, 1)])
+def test_degenerate_volumes(kats, torch, shape):
+    """Volumes one voxel wide, high or deep: partly empty 16 x 16 x 16 tiles, single slices, a
+    single voxel column; recon and adjoint against the oracle, host path bit for bit."""
+    import synth
+    cfg = dict(synth.config(1))
+    cfg.update(nx=shape[0], ny=shape[1], nz=shape[2])
+    g = oracle.derive_geometry(cfg)
+    sino = np.random.default_rng(sum(shape)).normal(size=(g["n_views"], g["n_rows"], g["n_cols"])).astype(np.float32)
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    assert kp.info["update_count"] == op.update_count()
+    dsino = torch.from_numpy(sino).cuda()
+    vol = kp.recon(dsino).cpu().numpy()
+    assert vol.shape == (shape[2], shape[1], shape[0])
+    assert rel_l2(vol, op.recon(sino.astype(np.float64))) < TOL
+    y = np.random.default_rng(1).normal(size=kp.vol_shape).astype(np.float32)
+    got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel_l2(got, op.adjoint(y.astype(np.float64))) < TOL
+    hv = torch.empty(kp.vol_shape, dtype=torch.float32).pin_memory()
+    kp.recon_host(torch.from_numpy(sino).pin_memory(), hv)
+    assert np.array_equal(hv.numpy(), vol)
+
+
 def test_device_status_clean(c1, kats):
     _, _, _, kp = c1
     assert kats.native.katsevich_device_status(kp.handle) == 0
