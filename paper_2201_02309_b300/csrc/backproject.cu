@@ -960,35 +960,33 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject_T(BPArgs a, const 
 // voxel columns x 16 slices adds its four bilinear taps per (voxel, view) into
 // the view's detector window in shared memory (the window the forward kernel
 // stages), then adds the window's non-zero entries to g^F with one global
-// atomic each.  The window holds fixed point in two 32-bit integer planes
-// (native integer shared atomics; float and 64-bit ones are compare-and-swap
-// loops, 8-10 times slower here): each CTA scales by a power of two 2^s chosen
-// from its largest possible contribution c_max < 2^e, s = 18 - e; a
-// contribution x adds h = round(x 2^s) to the high plane and
-// round((x 2^s - h) 2^12) to the low plane.  One window entry takes at most
-// 4096 contributions, so the planes stay below 2^30 and 2^23, and the
-// quantum is 2^-30 c_max.  Two windows alternate (one filling,
-// one draining), one CTA barrier per view; the window's first column per view
-// is computed at the tile corners one view ahead.
+// atomic each.  The window holds 32-bit fixed point (native integer shared
+// atomics; float and 64-bit ones are compare-and-swap loops, 8-10 times slower
+// here).  A thread first sums its slices' taps per detector row in registers
+// (the rows rise with z), so it deposits into a window entry at most once per
+// view, at most K taps per deposit (K from the smallest row step per slice,
+// two per slice sharing the row).  The CTA's warps form G groups, each with
+// its own copy of the window, so a copy's entry takes at most 256 / G
+// deposits per view; with 2^hb >= (256 / G) K and the CTA's largest possible
+// tap c_max < 2^e, the CTA scales by 2^s, s = 30 - hb - e, and a copy's entry
+// stays below 2^30.  The drain adds the G copies in 64-bit integers.  Taps on
+// clamped (off-detector) rows may wrap; those entries are never added to g^F.
+// The quantum is 2^(hb-30) c_max (2^-22 c_max for the clinical scanners at
+// G = 4).  Two windows alternate (one filling, one draining), one CTA barrier
+// per view; the window's first column per view is computed at the tile
+// corners one view ahead.
 constexpr int BT_THREADS = B2_TX * B2_TY;
 
-// x (already scaled, |x| < 2^18, or the sum of at most three such on one
-// row of one thread) into the high plane at p and its rounding remainder,
-// times 2^12, into the low plane at p + plane.
-__device__ __forceinline__ void deposit(int *p, int plane, float x)
-{
-    const int h = __float2int_rn(x);
-    atomicAdd(p, h);
-    atomicAdd(p + plane, __float2int_rn((x - (float)h) * 4096.0f));
-}
+// x (already scaled: at most K taps of magnitude below 2^(30 - hb)) into the window at p.
+__device__ __forceinline__ void deposit(int *p, float x) { atomicAdd(p, __float2int_rn(x)); }
 
 template <int PITCH, bool POLY, bool ROWS_OK>
 __global__ void __launch_bounds__(BT_THREADS, 2)
-    k_backproject_T_win(BPArgs a, int W, int srows, int slot_floats, float out_scale, float inv_v_max,
-                        const float *__restrict__ vol, float *gF)
+    k_backproject_T_win(BPArgs a, int W, int srows, int slot_floats, float out_scale, float inv_v_max, int hb,
+                        int G, const float *__restrict__ vol, float *gF)
 {
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-    extern __shared__ int win[];  // [2 windows][2 planes][slot_floats] fixed-point sums
+    extern __shared__ int win[];  // [2 windows][G copies][slot_floats] fixed-point sums
     __shared__ int s_col[3];
     // staged rows [s_rlo, s_rhi] touched in view j, slot j % 3 (reset two views ahead of its use)
     __shared__ int s_rlo[3], s_rhi[3];
@@ -1052,15 +1050,15 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     for (int t = 0; t < B2_T; ++t) fm = fmaxf(fm, fabsf(f[t]));
     for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
     if (lane == 0) s_fmax[warp] = fm;
-    for (int e = tid; e < 4 * slot_floats; e += BT_THREADS) win[e] = 0;
+    for (int e = tid; e < 2 * G * slot_floats; e += BT_THREADS) win[e] = 0;
     __syncthreads();
-    // fixed-point scale: 2^(18 - e) with the largest contribution below 2^e
+    // fixed-point scale: 2^(30 - hb - e) with the largest tap below 2^e
     fm = 0.0f;
     for (int w8 = 0; w8 < BT_THREADS / 32; ++w8) fm = fmaxf(fm, s_fmax[w8]);
     int ex = 0;
     frexpf(fm * inv_v_max, &ex);
-    const float scale = fm > 0.0f ? exp2f((float)min(18 - ex, 126)) : 0.0f;
-    const float inv_scale = fm > 0.0f ? exp2f(-(float)min(18 - ex, 126)) : 0.0f;
+    const float scale = fm > 0.0f ? exp2f((float)min(30 - hb - ex, 126)) : 0.0f;
+    const float inv_scale = fm > 0.0f ? exp2f(-(float)min(30 - hb - ex, 126)) : 0.0f;
     if (kmin <= kmax) {
         atomicMin(&s_K0, kmin);
         atomicMax(&s_K1, kmax);
@@ -1121,7 +1119,8 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
             float fc;
             column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
             KATS_DCHECK(ci - s_col[j % 3] >= 0 && ci - s_col[j % 3] <= W - 2, 4);
-            const uint32_t colx = (uint32_t)(2 * b * slot_floats + min(max(ci - s_col[j % 3], 0), W - 2)) -
+            const uint32_t colx = (uint32_t)((b * G + (warp & (G - 1))) * slot_floats +
+                                             min(max(ci - s_col[j % 3], 0), W - 2)) -
                                   (0x4B000000u << SH);
             const float M = a.D * rsqrtf(fmaf(u, u, v * v));
             const float kf = (float)(k - kbase);
@@ -1155,16 +1154,16 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 if (q != qa) {
                     if (qa == kNone) q_first = q;
                     if (qa != kNone) {
-                        deposit(win + qa, slot_floats, a0);
-                        deposit(win + qa + 1, slot_floats, a1);
+                        deposit(win + qa, a0);
+                        deposit(win + qa + 1, a1);
                     }
                     if (qa != kNone && q == qa + PITCH) {  // down one row: the old bottom row becomes the top
                         a0 = b0;
                         a1 = b1;
                     } else {
                         if (qa != kNone) {
-                            deposit(win + qa + PITCH, slot_floats, b0);
-                            deposit(win + qa + PITCH + 1, slot_floats, b1);
+                            deposit(win + qa + PITCH, b0);
+                            deposit(win + qa + PITCH + 1, b1);
                         }
                         a0 = a1 = 0.0f;
                     }
@@ -1177,10 +1176,10 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
                 b1 = fmaf(bot, fc, b1);
             }
             if (qa != kNone) {
-                deposit(win + qa, slot_floats, a0);
-                deposit(win + qa + 1, slot_floats, a1);
-                deposit(win + qa + PITCH, slot_floats, b0);
-                deposit(win + qa + PITCH + 1, slot_floats, b1);
+                deposit(win + qa, a0);
+                deposit(win + qa + 1, a1);
+                deposit(win + qa + PITCH, b0);
+                deposit(win + qa + PITCH + 1, b1);
                 const uint32_t base = colx + (0x4B000000u << SH);  // window offset of staged row 0
                 r_first = (int)((q_first - base) >> SH);
                 r_last = (int)((qa - base) >> SH) + 1;
@@ -1196,19 +1195,22 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
         __syncthreads();  // window b of view k is complete; window b^1 (view k-1) has been drained
         // drain window b into g^F: staged row 0 is detector row -1, columns from s_col
         const int col0 = s_col[j % 3];
-        int *w = win + 2 * b * slot_floats;
+        int *w = win + b * G * slot_floats;
         float *view = gF + (int64_t)(k - a.first_view) * per_view;
         // only the staged rows some thread deposited into can be nonzero
         const int rlo = s_rlo[j % 3], rhi = s_rhi[j % 3];
         const int e_end = rhi >= 0 ? min((rhi + 1) * PITCH, wsize) : 0;
         for (int e = (rhi >= 0 ? rlo * PITCH : 0) + tid; e < e_end; e += BT_THREADS) {
-            const int hi = w[e], lo = w[e + slot_floats];
-            if ((hi | lo) == 0) continue;
-            w[e] = 0;
-            w[e + slot_floats] = 0;
+            long long q = 0;
+            for (int gi = 0; gi < G; ++gi) {
+                int *we = w + gi * slot_floats + e;
+                q += *we;
+                *we = 0;
+            }
+            if (q == 0) continue;
             const int r = e / PITCH - 1, c = col0 + e % PITCH;
             if (r >= 0 && r < a.n_rows && c >= 0 && c < a.n_cols)
-                atomicAdd(view + r * a.gcols + c, fmaf((float)lo, 1.0f / 4096.0f, (float)hi) * inv_scale);
+                atomicAdd(view + r * a.gcols + c, (float)q * inv_scale);
         }
     }
 }
@@ -1220,8 +1222,22 @@ static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, 
     *launched = false;
     const int srows = (int)p.g.n_rows + 3;
     const int slot = (PITCH * srows + 31) / 32 * 32;
-    const size_t smem = sizeof(int) * (size_t)slot * 4;
+    // window copies: 4 where two CTAs per SM still fit, else 2, else 1
+    auto ring_bytes = [&](int copies) { return sizeof(int) * (size_t)slot * 2 * copies; };
+    const int G = ring_bytes(4) <= 100 * 1024 ? 4 : (ring_bytes(2) <= 100 * 1024 ? 2 : 1);
+    const size_t smem = ring_bytes(G);
     if (W > PITCH || smem > 100 * 1024 || p.n_fviews >= INT32_MAX || !(p.g.R > p.r_fov)) return KATS_OK;
+    // headroom: a row step per slice of at least dur_min = D / (R + r_max) dz / d_w puts at most
+    // floor(1 / dur_min) + 1 of a thread's slices on one row, two taps each (that row as top or bottom)
+    const kats_geometry &g = p.g;
+    const double xa = fabs(g.x0 - 0.5 * g.dx), xb = fabs(g.x0 + ((double)g.nx - 0.5) * g.dx);
+    const double ya = fabs(g.y0 - 0.5 * g.dy), yb = fabs(g.y0 + ((double)g.ny - 0.5) * g.dy);
+    const double r_max = std::hypot(std::max(xa, xb), std::max(ya, yb));
+    const double dur_min = g.D / (g.R + r_max) * g.dz / g.d_w;
+    if (!(dur_min > 0.0)) return KATS_OK;
+    const double taps = 2.0 * (std::floor(1.0 / dur_min) + 1.0);
+    const int hb = (int)std::ceil(std::log2((double)(BT_THREADS / G) * taps));
+    if (hb > 24) return KATS_OK;  // quantum coarser than 2^-6 c_max: leave it to the global-atomic kernel
     const bool poly = p.r_fov <= p.g.R * 0.70710678;
     const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
@@ -1233,7 +1249,8 @@ static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, 
               (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
     // 1/v* <= 1/(R - r_fov) for every voxel column, rounded up
     const float inv_v_max = (float)(1.0 / (p.g.R - p.r_fov)) * 1.0001f;
-    kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, vol, gF);
+    kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, hb, G, vol,
+                                         gF);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *launched = true;
