@@ -497,6 +497,10 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             kfull_lo = max(kfull_lo, ka[t]);
             kfull_hi = min(kfull_hi, kb[t]);
         }
+        if (!p.mono) {  // windows not monotone in the slice: no full range and no ramp walk
+            kfull_lo = INT32_MAX;
+            kfull_hi = INT32_MIN;
+        }
         const int kbase = active ? kmin : 0;
 #pragma unroll
         for (int t = 0; t < B2_T / 2; ++t) acc2[t] = make_float2(0.0f, 0.0f);
@@ -640,12 +644,13 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                     (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - col0, 0), p.W - 2)) -
                     (0x4B000000u << SH);
                 // full: every slice inside its window with weight 1; ramps: windows
-                // still opening (no slice ended) or closing (every slice started)
+                // still opening (no slice ended) or closing (every slice started); a plan
+                // without monotone windows has an empty full range (every view general)
                 if (k > kfull_lo && k < kfull_hi)
                     bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
-                else if (p.mono && k < kfull_hi)
+                else if (k < kfull_hi)
                     bp_view_ramp<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
-                else if (p.mono && k > kfull_lo)
+                else if (k > kfull_lo)
                     bp_view_ramp<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi,
                                                                acc2);
                 else
