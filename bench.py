@@ -44,6 +44,8 @@ def parse():
                     help="N > 1: one volume per rank (weak scaling) or one volume split into z-slabs (strong)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="config 2: leave the precision, differentiation and serving forms out of the JSON line")
     ap.add_argument("--nz", type=int, default=None, help="smaller volume height (profiling captures only)")
     ap.add_argument("--turns", type=int, default=None, help="fewer helix turns (profiling captures only)")
     ap.add_argument("--simulate", action="store_true", help="time the data-simulation pipeline instead")
@@ -147,49 +149,70 @@ def workload(cfg_index, geom, cfg):
     return cfg, sino.astype(np.float32)
 
 
-def describe(cfg, g, info, precision="fp32"):
+def describe(cfg, g, info, world=1, slabs=False):
+    """The workload (identical on both arms of the benchmark; the arithmetic type is the line's dtype)."""
     return {"workload": cfg["name"], "volume_xyz": [g["nx"], g["ny"], g["nz"]], "voxel_mm": g["dx"],
             "detector_rows_cols": [g["n_rows"], g["n_cols"]], "views": g["n_views"],
             "views_per_turn": g["views_per_turn"], "pitch_mm": g["P"], "R_mm": g["R"], "D_mm": g["D"],
             "slices_per_pitch": info["slices_per_pitch"], "n_psi": info["n_psi"],
             "filtered_views": info["n_filtered_views"], "updates_per_volume": info["update_count"],
-            "precision": precision, "batch_per_gpu": 1,
-            "l2": "inputs larger than L2 (sinogram %.2f GB, filter workspace %.2f GB)" % (
-                g["n_views"] * g["n_rows"] * g["n_cols"] * 4 / 1e9, info["workspace_bytes"] / 1e9)}
+            "batch_per_gpu": 1, "parallelism": f"z-slabs x{world}" if slabs else f"replicas x{world}",
+            "l2": "inputs larger than L2 (sinogram %.2f GB, filtered view window %.2f GB)" % (
+                g["n_views"] * g["n_rows"] * g["n_cols"] * 4 / 1e9,
+                info["n_filtered_views"] * g["n_rows"] * g["n_cols"] * 4 / 1e9)}
 
 
 # --------------------------------------------------------------------------- oracle
-def oracle_sample(g, sino, info, n_views=96, n_vox=65536, seed=0):
+def oracle_sample(g, sino, info, n_filter_views=128):
     """Time the FP64 oracle, as it stands, on a bounded sample of the workload and
-    extrapolate to one full reconstruction: filter time per view x filtered
-    views + backprojection time per update x update count."""
+    extrapolate to one full reconstruction: the backprojection of one whole slice
+    (every voxel of slice nz/2 over its own PI window) and the filter (steps 1-6) on
+    n_filter_views of the views that slice reads; filter time per view x filtered
+    views + backprojection time per update x update count.  The filter does the same
+    work for every view, so a block of views stands for all of them."""
     import numpy as np
 
     import oracle
-    rng = np.random.default_rng(seed)
     op = oracle.Plan(g, with_pi=False)
-    v0 = info["first_view"] + info["n_filtered_views"] // 2
-    t = time.perf_counter()
-    gF_part = op.filter(sino.astype(np.float64), v0, n_views)
-    t_filter = time.perf_counter() - t
     s = g["nz"] // 2
-    ijk = np.stack([rng.integers(0, g["nx"], n_vox), rng.integers(0, g["ny"], n_vox), np.full(n_vox, s)], 1)
+    ii, jj = np.meshgrid(np.arange(g["nx"]), np.arange(g["ny"]), indexing="xy")
+    ijk = np.stack([ii.ravel(), jj.ravel(), np.full(ii.size, s)], 1)
     win = oracle.pi_windows(g, ijk)
     a, b = int(win[0].min()), int(win[1].max())
+    nf = min(n_filter_views, b - a + 1)
+    v0 = (a + b - nf) // 2  # a block of views from the middle of the slice's window
+    t = time.perf_counter()
+    gF_part = op.filter(sino, v0, nf)
+    t_filter = time.perf_counter() - t
     gF = np.zeros((b - a + 1, g["n_rows"], g["n_cols"]))
-    k = min(n_views, gF.shape[0])
-    gF[:k] = gF_part[:k]
+    gF[v0 - a:v0 - a + nf] = gF_part
     t = time.perf_counter()
     oracle.backproject_points(g, gF, a, ijk, win)
     t_bp = time.perf_counter() - t
     upd = int((win[1] - win[0] + 1).sum())
-    est = t_filter / n_views * info["n_filtered_views"] + t_bp / upd * info["update_count"]
+    est = t_filter / nf * info["n_filtered_views"] + t_bp / upd * info["update_count"]
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": info["update_count"] / est / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle (C, OpenMP) on {n_views} filtered views ({t_filter:.1f} s) and {n_vox} voxels "
-                      f"of slice {s} ({upd} updates, {t_bp:.1f} s), extrapolated to one full volume "
-                      f"({est:.0f} s)",
+            "sample": f"FP64 oracle (C, OpenMP, {cores} threads): backprojection of all {ijk.shape[0]} voxels of "
+                      f"slice {s} over their PI windows ({upd} updates, {t_bp:.1f} s) and the filter on {nf} of "
+                      f"the {b - a + 1} views that slice reads ({t_filter:.1f} s), extrapolated linearly in "
+                      f"updates and filtered views to one full volume ({est:.0f} s)",
             "seconds": t_filter + t_bp}
+
+
+def oracle_patch(g, sino, s, x0, y0, n=16):
+    """The oracle's values of an n x n patch of slice s (every view those voxels read
+    filtered by the oracle): the reference the reduced-precision forms are measured
+    against at full size.  Returns (ijk, values)."""
+    import numpy as np
+
+    import oracle
+    ii, jj = np.meshgrid(np.arange(x0, x0 + n), np.arange(y0, y0 + n), indexing="xy")
+    ijk = np.stack([ii.ravel(), jj.ravel(), np.full(ii.size, s)], 1)
+    win = oracle.pi_windows(g, ijk)
+    a, b = int(win[0].min()), int(win[1].max())
+    gF = oracle.Plan(g, with_pi=False).filter(sino, a, b - a + 1)
+    return ijk, oracle.backproject_points(g, gF, a, ijk, win)
 
 
 def run_reference(args):
@@ -212,7 +235,7 @@ def run_reference(args):
     _, sino = workload(args.config, g, cfg)
     vals = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(g, sino, info, n_views=16, n_vox=8192, seed=i)
+        r = oracle_sample(g, sino, info)
         if i >= args.warmup:
             vals.append(r)
     v = statistics.median(x["value"] for x in vals)
@@ -220,7 +243,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": describe(cfg, g, info, "fp64"),
+            "config": describe(cfg, g, info, args.gpus),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -399,19 +422,85 @@ def run_ours(args):
         cpu = oracle_sample(g, sino_np, info)
         cpu.pop("seconds", None)
 
+    forms = None
+    if rank == 0 and world == 1 and not slabs and not args.no_forms and args.precision == "fp32" and \
+            args.config == 2 and not args.nz and not args.turns:
+        forms = other_forms(args, plan, g, sino, sino_np, vol, ws, ms)
+
     if rank == 0:
-        config = describe(cfg, g, info, args.precision)
-        config["parallelism"] = f"z-slabs x{world}" if slabs else f"replicas x{world}"
+        config = describe(cfg, g, info, world, slabs)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "strong" if slabs else "weak",
                 "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
                 "data": "synthetic", "config": config, "vol_per_s": volumes / (ms / 1e3),
+                "workspace_bytes": info["workspace_bytes"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
+        if forms is not None:
+            line.update(forms)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- other forms
+def other_forms(args, plan, g, sino, sino_np, vol32, ws32, ms32):
+    """The three other forms of the operator, measured in the same run as the FP32 line:
+    BF16 / FP16 storage on the same workload (device step, GUPS, ratio to the FP32 step, and
+    accuracy against the FP64 oracle on a 16 x 16 voxel patch of the middle slice: rel-L2 and
+    max-abs, beside the FP32 path's own); config 3 forward + backward of the differentiable layer
+    (batch 4); the serving mix saturated and at rho = 0.8, with served over plain FP32."""
+    import numpy as np
+    import torch
+
+    import paper_2201_02309_b300 as kats
+    dev = sino.device
+    stream = torch.cuda.current_stream(dev)
+    upd = plan.info["update_count"]
+    s, x0, y0 = g["nz"] // 2, 3 * g["nx"] // 8, g["ny"] // 4
+    ijk, want = oracle_patch(g, sino_np, s, x0, y0)
+
+    def accuracy(v):
+        got = v[ijk[:, 2], ijk[:, 1], ijk[:, 0]].astype(np.float64)
+        return {"rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                "max_abs": float(np.abs(got - want).max()), "max_abs_over_max": float(
+                    np.abs(got - want).max() / np.abs(want).max())}
+
+    prec_out = {"oracle_sample": f"16 x 16 voxels of slice {s} at x, y >= ({x0}, {y0}), every view they read "
+                                 "filtered by the FP64 oracle",
+                "fp32": dict(ms_per_step=ms32, gups=upd / ms32 * 1e-6, **accuracy(vol32.cpu().numpy()))}
+    for name, p in (("fp16", kats.KATS_PREC_FP16), ("bf16", kats.KATS_PREC_BF16)):
+        ws = plan.workspace(precision=p, device=dev)
+        out = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            plan.recon(sino, out=out, workspace=ws, precision=p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.recon(sino, out=out, workspace=ws, precision=p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        prec_out[name] = dict(ms_per_step=ms, gups=upd / ms * 1e-6, over_fp32=ms32 / ms,
+                              **accuracy(out.cpu().numpy()))
+        del out
+    diff = differentiation_result(argparse.Namespace(steps=max(3, args.steps // 2), warmup=2))
+    srv = serving_result(argparse.Namespace(requests=args.requests, slots=args.slots, arena_gb=args.arena_gb,
+                                            plan_cache_gb=args.plan_cache_gb, precision="fp32"), rhos=(0.8,))
+    sv = srv["serving"]
+    return {"precision_forms": prec_out,
+            "differentiation": {"workload": diff["config"]["workload"], "batch": diff["config"]["batch"],
+                                "forward_ms": diff["forward_ms"], "backward_ms": diff["backward_ms"],
+                                "ms_per_batch": diff["ms_per_step"], "gups_fwd_bwd": diff["value"],
+                                "gpu_launches": diff["gpu_launches"]},
+            "serving": {"workload": srv["config"]["workload"], "requests": srv["config"]["requests"],
+                        "slots": srv["config"]["slots"], "saturated": sv["saturated"],
+                        "rho_0.8": sv["poisson"]["0.8"], "plain_fp32_vol_per_s": sv["plain_fp32"]["vol_per_s"],
+                        "served_over_plain": sv["served_over_plain"],
+                        "rho_0.8_over_plain": sv["poisson"]["0.8"]["vol_per_s"] / sv["plain_fp32"]["vol_per_s"],
+                        "gpu_launches": srv["gpu_launches"]}}
 
 
 # ----------------------------------------------------------------- serving form
@@ -445,6 +534,10 @@ def serving_protocols(kats, n_protocols=12, seed=7):
 
 
 def run_serving(args):
+    print(json.dumps(serving_result(args)))
+
+
+def serving_result(args, rhos=(0.5, 0.8, 1.0)):
     """Config 5: a seeded Poisson stream of requests over mixed protocols,
     served with continuous batching; p50/p99 latency and vol/s, next to the
     plain FP32 path (one request at a time through katsevich_recon_host)."""
@@ -538,7 +631,7 @@ def run_serving(args):
     clocks.start()
     lat_sat, span_sat, st_sat = serve(None, True)
     runs = {}
-    for rho in (0.5, 0.8, 1.0):
+    for rho in rhos:
         gaps = np.random.default_rng(seed).exponential(1.0 / (rho * mu), size=n_req)
         lat, span, st = serve(np.cumsum(gaps) - gaps[0], False)
         runs[str(rho)] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -564,11 +657,15 @@ def run_serving(args):
         },
         "gpu_launches": st_sat["launches"], "clocks": clk,
     }
-    print(json.dumps(line))
+    return line
 
 
 # ----------------------------------------------------------- differentiation
 def run_differentiation(args):
+    print(json.dumps(differentiation_result(args)))
+
+
+def differentiation_result(args):
     """Config 3: the operator as a differentiable layer.  One step = forward
     (steps 1-7) and backward (the hand-written adjoint) of a batch of 4
     sinograms of the sparse-detector scanner (368 columns, 580 views/turn,
@@ -617,7 +714,7 @@ def run_differentiation(args):
                        "pitch_mm": g["P"], "updates_per_volume": upd / B},
             "forward_ms": fwd, "backward_ms": bwd, "forward_gups": upd / fwd * 1e-6, "backward_gups": upd / bwd * 1e-6,
             "gpu_launches": launches, "clocks": clk}
-    print(json.dumps(line))
+    return line
 
 
 # ----------------------------------------------------------- data simulation

@@ -451,6 +451,21 @@ KATS_API int katsevich_debug_check_flags(int *flags);
  * columns narrower than its tile needs, so that the column check fires; taps
  * stay clamped inside the window, results are wrong, nothing faults.  0 ends it. */
 KATS_API void katsevich_debug_narrow_window(int cols);
+/* Checked build only (a no-op otherwise): launch the backprojection as if the plan's PI windows
+ * were not monotone in z (on != 0), so every view takes the general end-weight path instead of
+ * the ramp walk; the result must not change.  0 ends it. */
+KATS_API void katsevich_debug_nonmonotone(int on);
+/* Checked build only (no-ops returning KATS_OK otherwise), for the test of the device-timeout
+ * path, set on the current device:
+ * katsevich_debug_wait_limit: the staged backprojection's bounded mbarrier waits give up after
+ *   `polls` polls instead of 2^22 (<= 0 restores the default);
+ * katsevich_debug_stall_producer: its producer warp stops issuing view pairs after `pairs` of
+ *   them (arming no further copy), so the consumers' waits run out, the CTA records
+ *   KATS_ETIMEOUT in the plan's device status (katsevich_device_status) and retires with no
+ *   copy in flight; the volume is then incomplete.  A negative value ends it.
+ * Errors: KATS_ECUDA. */
+KATS_API int katsevich_debug_wait_limit(int polls);
+KATS_API int katsevich_debug_stall_producer(int pairs);
 
 /*
  * Number of kernels the library has launched in this process so far (every

@@ -205,6 +205,17 @@ constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
 constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
 
+#ifdef KATS_DEBUG_CHECKS
+// Checked build only, for the test of the timeout path: a lower poll limit, and a producer that
+// stops issuing after this many view pairs (-1: never), so that the consumers' waits run out
+// without any copy in flight.  Set by katsevich_debug_wait_limit / katsevich_debug_stall_producer.
+__device__ int g_debug_wait_limit = kWaitLimit;
+__device__ int g_debug_stall_pairs = -1;
+#define KATS_BP_WAIT_LIMIT ::kats::g_debug_wait_limit
+#else
+#define KATS_BP_WAIT_LIMIT kWaitLimit
+#endif
+
 // arctan(t) ~= t * P(t^2) on |t| <= 1: odd minimax polynomial of degree 17
 // fitted by csrc/gen_atan_poly.py (max abs error 5.8e-9 in exact arithmetic,
 // 1.0e-7 with FP32 Horner evaluation, about the error of atanf).
@@ -257,7 +268,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // Bounded wait on an mbarrier phase; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
-    for (int i = 0; i < kWaitLimit; ++i)
+    for (int i = 0; i < KATS_BP_WAIT_LIMIT; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -563,6 +574,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
         bool ok = true;
         for (int j = 0; j < nviews; j += 2) {
+#ifdef KATS_DEBUG_CHECKS
+            if (g_debug_stall_pairs >= 0 && j / 2 >= g_debug_stall_pairs) break;  // test hook: stop issuing
+#endif
             if (j >= 2 * RP && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
                 ok = false;
                 break;
@@ -599,11 +613,15 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             }
             kmod = kmod1 + 1 == a.vpt ? 0 : kmod1 + 1;
         }
-        if (!ok && lane == 0) {
-            // let every issued copy land before the CTA's shared memory is released
+        if (lane == 0) {
+            // Every copy this CTA issued lands before the producer warp retires, on every exit
+            // path: consumers that give up on a wait return early, and the CTA (and its shared
+            // memory) must not retire under a bulk copy still in flight.  Pairs before the last
+            // RP were released by the consumers (so landed) or the empty wait above gave up.
+            bool landed = true;
             for (int i = max(0, issued - RP); i < issued; ++i)
-                mbar_wait(&s_full[i % RP], (uint32_t)((i / RP) & 1));
-            atomicExch(p.status, kDevStatusTimeout);
+                landed = mbar_wait(&s_full[i % RP], (uint32_t)((i / RP) & 1)) && landed;
+            if (!ok || !landed) atomicExch(p.status, kDevStatusTimeout);
         }
         return;
     }
@@ -621,9 +639,10 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     for (int j = 0; j < nviews; j += 2) {
         const int kA = K0 + j, kB = kA + 1;
         const bool hasB = j + 1 < nviews;
-        if (!mbar_wait(&s_full[ps], phase)) {
+        // warp-uniform: a wait that ends at the limit for some lanes only still stops the warp
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_full[ps], phase))) {
             if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
-            return;  // the producer's own bounded waits end the CTA
+            return;  // the producer retires only after its issued copies have landed
         }
         const bool onA = active && kA >= kvmin && kA <= kvmax;
         const bool onB = hasB && active && kB >= kvmin && kB <= kvmax;
@@ -750,6 +769,9 @@ static EncodeTiledFn encode_fn()
 // Checked build only: columns taken off every staged window, so that a test can see the column
 // check fire (the taps stay clamped inside the window, the result is wrong, nothing faults).
 static std::atomic<int> g_debug_narrow{0};
+// Checked build only: launch as if the plan's PI windows were not monotone in z (every view takes
+// the general end-weight path), so that a test can compare that path with the ramp walk.
+static std::atomic<int> g_debug_nonmono{0};
 
 // Staged window width: the tile's columns (B2_TX x B2_TY voxel centres) subtend at
 // most 2 atan(L / 2 d) with L the tile diagonal and d = R - r_fov the nearest
@@ -806,7 +828,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return KATS_OK;
     BP2Args b{a, W, srows, slot, p.dev_status, (float)(p.dlam / (2.0 * kPi) / (MODE == 0 ? 1.0 : p.g.d_alpha)),
-              p.pi_monotone ? 1 : 0};
+              p.pi_monotone && !g_debug_nonmono.load() ? 1 : 0};
     // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
     const bool poly = p.r_fov <= p.g.R * 0.70710678;
     // every contributing row within half a row of the detector (plan extents, FP32 on device)
@@ -1306,6 +1328,37 @@ void katsevich_debug_narrow_window(int cols)
 #else
     (void)cols;
 #endif
+}
+
+void katsevich_debug_nonmonotone(int on)
+{
+#ifdef KATS_DEBUG_CHECKS
+    kats::g_debug_nonmono.store(on ? 1 : 0);
+#else
+    (void)on;
+#endif
+}
+
+int katsevich_debug_wait_limit(int polls)
+{
+#ifdef KATS_DEBUG_CHECKS
+    const int v = polls > 0 ? polls : kats::kWaitLimit;
+    KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_wait_limit, &v, sizeof(int)));
+#else
+    (void)polls;
+#endif
+    return KATS_OK;
+}
+
+int katsevich_debug_stall_producer(int pairs)
+{
+#ifdef KATS_DEBUG_CHECKS
+    const int v = pairs >= 0 ? pairs : -1;
+    KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_stall_pairs, &v, sizeof(int)));
+#else
+    (void)pairs;
+#endif
+    return KATS_OK;
 }
 
 int katsevich_debug_check_flags(int *flags)

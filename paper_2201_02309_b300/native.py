@@ -32,7 +32,8 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_noise_workspace_bytes", "katsevich_add_noise", "katsevich_smem_read_bandwidth",
            "katsevich_tex_bilinear_rate",
            "katsevich_launch_count", "katsevich_debug_checks_enabled", "katsevich_debug_check_flags",
-           "katsevich_debug_narrow_window"]
+           "katsevich_debug_narrow_window", "katsevich_debug_nonmonotone", "katsevich_debug_wait_limit",
+           "katsevich_debug_stall_producer"]
 
 
 class kats_geometry(ctypes.Structure):
@@ -122,6 +123,9 @@ def load() -> ctypes.CDLL:
         "katsevich_debug_checks_enabled": (ctypes.c_int, []),
         "katsevich_debug_check_flags": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
         "katsevich_debug_narrow_window": (None, [ctypes.c_int]),
+        "katsevich_debug_nonmonotone": (None, [ctypes.c_int]),
+        "katsevich_debug_wait_limit": (ctypes.c_int, [ctypes.c_int]),
+        "katsevich_debug_stall_producer": (ctypes.c_int, [ctypes.c_int]),
         "katsevich_device_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_backproject_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
         "katsevich_filter_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P]),
@@ -292,6 +296,21 @@ def katsevich_debug_check_flags() -> int:
 def katsevich_debug_narrow_window(cols: int) -> None:
     """Checked build only: stage view windows `cols` columns too narrow (0 ends it)."""
     load().katsevich_debug_narrow_window(int(cols))
+
+
+def katsevich_debug_nonmonotone(on: bool) -> None:
+    """Checked build only: every view through the general end-weight path (False ends it)."""
+    load().katsevich_debug_nonmonotone(1 if on else 0)
+
+
+def katsevich_debug_wait_limit(polls: int) -> None:
+    """Checked build only: the staged backprojection's waits give up after `polls` polls (0: default)."""
+    check(load().katsevich_debug_wait_limit(int(polls)))
+
+
+def katsevich_debug_stall_producer(pairs: int) -> None:
+    """Checked build only: its producer stops issuing after `pairs` view pairs (-1 ends it)."""
+    check(load().katsevich_debug_stall_producer(int(pairs)))
 
 
 def katsevich_device_status(plan) -> int:

@@ -14,6 +14,24 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def max_abs_rel(a, b):
+    """Largest element error relative to the largest expected magnitude."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def check32(got, want, tol=1e-5, name=""):
+    """The FP32 parity bar: rel-L2 <= tol over the array and, element by element,
+    |got - want| <= tol * max|want|, so that a wrong tile corner or slice cannot hide
+    under the global norm.  Prints both figures."""
+    rel, mx = rel_l2(got, want), max_abs_rel(got, want)
+    print(f"{name} rel-L2 {rel:.2e}, max-abs / max {mx:.2e}")
+    assert rel <= tol, f"{name} rel-L2 {rel:.3e} > {tol:g}"
+    assert mx <= tol, f"{name} max-abs error {mx:.3e} x max|want| > {tol:g}"
+    return rel, mx
+
+
 def c1_case():
     cfg = synth.config(1)
     g = oracle.derive_geometry(cfg)

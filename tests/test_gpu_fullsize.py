@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from cases import near_tie, rel_l2
+from cases import check32, near_tie, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -57,7 +57,7 @@ def test_c2_filtered_views_sampled(c2):
     v0 = kp.info["first_view"]
     for v in (0, 1777, kp.info["n_filtered_views"] - 1):
         want = op.filter(sino.astype(np.float64), v0 + v, 1)[0]
-        assert rel_l2(gF[v, :, :g["n_cols"]].cpu().numpy(), want) < TOL
+        check32(gF[v, :, :g["n_cols"]].cpu().numpy(), want)
 
 
 def test_c2_voxels_sampled(c2):
@@ -74,7 +74,7 @@ def test_c2_voxels_sampled(c2):
     gF = op.filter(sino.astype(np.float64), v0, v1 - v0 + 1)
     want = oracle.backproject_points(g, gF, v0, ijk, (ka, kb, wa, wb))
     got = vol[ijk[:, 2], ijk[:, 1], ijk[:, 0]]
-    assert rel_l2(got, want) < TOL
+    check32(got, want)
     assert np.isfinite(vol).all()
     assert kp.info["update_count"] > 4.0e10
     import paper_2201_02309_b300 as kats
@@ -122,3 +122,107 @@ def test_host_pipeline_small_volume_long_window(prec):
     kp.recon_host(hs, hv, precision=p)
     assert np.array_equal(hv.numpy(), dev)
     assert np.isfinite(dev).all() and np.abs(dev).max() > 0
+
+
+def compare_int_table(got, want, want_frac, name):
+    """Integer table bit for bit; a mismatch is allowed only at a floor tie (the oracle's
+    fraction within 1e-9 of an integer).  Returns (mismatches, ties seen)."""
+    bad = got != want
+    ties = near_tie(want_frac)
+    assert not (bad & ~ties).any(), f"{name}: {int((bad & ~ties).sum())} mismatches away from ties"
+    print(f"{name}: {int(bad.sum())} mismatches, {int(ties.sum())} near-ties of {got.size}")
+    return int(bad.sum()), int(ties.sum())
+
+
+def compare_kappa_psi(kp, op):
+    # the backward-rebinning root psi_hat with the smallest |psi| (Sec. II, Eq. (w_k)): the
+    # device's safeguarded Newton against the oracle's bisection, on every detector sample
+    compare_int_table(kp.table("kappa_idx"), op.kap[0], op.kap[1], "kappa_idx")
+    same = kp.table("kappa_idx") == op.kap[0]
+    assert np.abs(kp.table("kappa_frac") - op.kap[1])[same].max() < 2e-7
+    compare_int_table(kp.table("psi_idx"), op.psi[0], op.psi[1], "psi_idx")
+    same = kp.table("psi_idx") == op.psi[0]
+    assert np.abs(kp.table("psi_frac") - op.psi[1])[same].max() < 2e-7
+
+
+def test_c2_kappa_psi_tables_clinical_fan(c2):
+    """The clinical fan (alpha_m = 0.654), where w_kappa turns over in psi and the
+    smallest-|psi| rule picks the root."""
+    g, _, kp, _, _ = c2
+    op = oracle.Plan(g, with_pi=False)
+    assert oracle.alpha_m(g) > 0.65
+    assert kp.table("psi_idx").shape == (64, 736) and kp.table("kappa_idx").shape == (128, 735)
+    compare_kappa_psi(kp, op)
+    # the smallest-root rule is exercised: detector samples whose w also has a second root
+    # further out on the same branch (past the turnover of w_kappa in psi)
+    assert second_root_samples(g, op) > 500
+
+
+def second_root_samples(g, op):
+    pm = 0.5 * np.pi + oracle.alpha_m(g)
+    idx, frac = op.psi
+    psi = -pm + (idx + frac) * (2 * pm / (oracle.n_psi(g) - 1))
+    nr, nc = idx.shape
+    alpha = (np.arange(nc) - 0.5 * (nc - 1)) * g["d_alpha"] + g["alpha_offset"]
+    w = (np.arange(nr) - 0.5 * (nr - 1)) * g["d_w"] + g["w_offset"]
+    n = 0
+    for c in range(nc):
+        end_hi, end_lo = oracle.w_kappa(g, alpha[c], pm), oracle.w_kappa(g, alpha[c], -pm)
+        for r in range(nr):
+            if idx[r, c] < 0:
+                continue
+            n += alpha[c] > 0 and psi[r, c] > 0 and w[r] >= end_hi
+            n += alpha[c] < 0 and psi[r, c] < 0 and w[r] <= end_lo
+    print(f"samples with a second, larger root: {n}")
+    return n
+
+
+SLICES_C2 = [0, 15, 16, 69, 70, 71, 139, 140, 255]
+
+
+def test_c2_pi_table_across_pitch_boundaries(c2):
+    """Slices on both sides of each pitch boundary read table slice s mod 70 with their
+    views shifted by (s div 70) turns: checked against the oracle's own PI solver for the
+    voxel itself (no table)."""
+    g, _, kp, _, _ = c2
+    rng = np.random.default_rng(11)
+    cols = [(0, 0), (511, 0), (0, 511), (511, 511), (15, 16), (16, 15), (255, 256), (256, 255)]
+    ijk = []
+    for s in SLICES_C2:
+        ijk += [(i, j, s) for i, j in cols]
+        ijk += [(int(i), int(j), s) for i, j in rng.integers(0, 512, (60, 2))]
+    ijk = np.array(ijk)
+    ka, kb, wa, wb = oracle.pi_windows(g, ijk)
+    N, vpt = 70, g["views_per_turn"]
+    k0, k1, w0, w1 = kp.table("k0"), kp.table("k1"), kp.table("w0"), kp.table("w1")
+    i, j, s = ijk[:, 0], ijk[:, 1], ijk[:, 2]
+    gk0 = k0[s % N, j, i] + (s // N) * vpt
+    gk1 = k1[s % N, j, i] + (s // N) * vpt
+    assert not ((gk0 != ka) & ~near_tie(wa)).any() and not ((gk1 != kb) & ~near_tie(wb)).any()
+    ok = (gk0 == ka) & (gk1 == kb)
+    assert np.abs(w0[s % N, j, i] - wa)[ok].max() < 2e-7 and np.abs(w1[s % N, j, i] - wb)[ok].max() < 2e-7
+
+
+def test_c2_voxels_boundary_slices(c2):
+    """Sampled voxels in the first and last 16-slice tiles, on both sides of the pitch
+    boundaries (69/70/71, 139/140) and of a 16 x 16 tile boundary, and the four corner
+    columns (the ones whose views take the longest ramps), against the oracle's chain on
+    exactly the views each group of slices needs."""
+    g, sino, kp, _, vol = c2
+    rng = np.random.default_rng(12)
+    op = oracle.Plan(g, with_pi=False)
+    cols = [(0, 0), (511, 0), (0, 511), (511, 511), (15, 15), (16, 16), (15, 16), (16, 15), (255, 256)]
+    got_all, want_all = [], []
+    for group in ([0, 15, 16], [69, 70, 71], [139, 140], [255]):
+        ijk = []
+        for s in group:
+            ijk += [(i, j, s) for i, j in cols]
+            ijk += [(int(i), int(j), s) for i, j in rng.integers(0, 512, (40, 2))]
+        ijk = np.array(ijk)
+        ka, kb, wa, wb = oracle.pi_windows(g, ijk)
+        v0, v1 = int(ka.min()), int(kb.max())
+        gF = op.filter(sino.astype(np.float64), v0, v1 - v0 + 1)
+        want_all.append(oracle.backproject_points(g, gF, v0, ijk, (ka, kb, wa, wb)))
+        got_all.append(vol[ijk[:, 2], ijk[:, 1], ijk[:, 0]])
+        check32(got_all[-1], want_all[-1], name=f"slices {group}")
+    check32(np.concatenate(got_all), np.concatenate(want_all), name="all boundary samples")
