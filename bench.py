@@ -499,7 +499,6 @@ def other_forms(args, plan, g, sino, sino_np, vol32, ws32, ms32):
                         "slots": srv["config"]["slots"], "saturated": sv["saturated"],
                         "rho_0.8": sv["poisson"]["0.8"], "plain_fp32_vol_per_s": sv["plain_fp32"]["vol_per_s"],
                         "served_over_plain": sv["served_over_plain"],
-                        "rho_0.8_over_plain": sv["poisson"]["0.8"]["vol_per_s"] / sv["plain_fp32"]["vol_per_s"],
                         "gpu_launches": srv["gpu_launches"]}}
 
 

@@ -27,6 +27,8 @@
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
 // iteration, so the slots go in pairs, each pair with one full / empty
 // mbarrier: one wait and one release per two views.  The ring holds RP
 // pairs, 3 or 2 (chosen at launch from the slot size).
-constexpr int B2_TX = 16, B2_TY = 16, B2_T = 16;
+constexpr int B2_TX = kTileX, B2_TY = kTileY, B2_T = 16;
 constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
 constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
@@ -216,13 +218,12 @@ __device__ int g_debug_stall_pairs = -1;
 #define KATS_BP_WAIT_LIMIT kWaitLimit
 #endif
 
-// arctan(t) ~= t * P(t^2) on |t| <= 1: odd minimax polynomial of degree 17
-// fitted by csrc/gen_atan_poly.py (max abs error 5.8e-9 in exact arithmetic,
-// 1.0e-7 with FP32 Horner evaluation, about the error of atanf).
-constexpr int kAtanTerms = 9;
-__constant__ float c_atan[kAtanTerms] = {2.456725342e-03f, -1.440136135e-02f, 3.978122771e-02f,
-                                         -7.234857976e-02f, 1.049894616e-01f, -1.416122913e-01f,
-                                         1.998590678e-01f, -3.333259821e-01f, 9.999998808e-01f};
+// The staged kernels measure a voxel's detector column from its tile centre's ray: with the
+// centre's (u_r, v_r) from the plan's table and the voxel's offset (du, dv) from it, the angle
+// between the two rays is atan(cross / dot), cross = du v_r - dv u_r, dot = r2 + du u_r + dv v_r,
+// small (|cross / dot| <= kTileTanMax) and formed without cancellation.  Its arctan is the Taylor
+// series to t^11 (truncation below t^13 / 13 <= 6e-10 at the bound).
+constexpr float kTileTanMax = 0.25f;
 
 struct BP2Args {
     BPArgs a;
@@ -232,6 +233,8 @@ struct BP2Args {
     int *status;
     float out_scale;  // dl / 2pi, divided by d_alpha for the scaled 16-bit storage
     int mono;         // window starts and ends nondecreasing in the slice (plan check)
+    const float4 *geo;  // the plan's tile-relative projection table [tile][view of a turn][2]
+    int geo_ntx;        // tiles per row of the table
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -282,18 +285,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// arctan(t) / d_alpha (t = u*/v*), the column coordinate before the alpha0 offset.
-template <bool POLY>
-__device__ __forceinline__ float angle_cols(const BPArgs &a, float t)
+// arctan(t) for |t| <= kTileTanMax: t (1 - t^2 / 3 + t^4 / 5 - t^6 / 7 + t^8 / 9 - t^10 / 11)
+__device__ __forceinline__ float atan_small(float t)
 {
-    if (POLY) {
-        const float s = t * t;
-        float p = c_atan[0];
-#pragma unroll
-        for (int i = 1; i < kAtanTerms; ++i) p = fmaf(p, s, c_atan[i]);
-        return t * p * a.inv_da;
-    }
-    return atanf(t) * a.inv_da;
+    const float s = t * t;
+    float p = fmaf(s, -1.0f / 11.0f, 1.0f / 9.0f);
+    p = fmaf(s, p, -1.0f / 7.0f);
+    p = fmaf(s, p, 1.0f / 5.0f);
+    p = fmaf(s, p, -1.0f / 3.0f);
+    return fmaf(t * s, p, t);
 }
 
 // Two slices' taps: bilinear samples at column colx + fc and rows ur2.x,
@@ -358,23 +358,30 @@ __device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2
 // it; a pair with neither slice in its window is skipped, one with a single
 // such slice still loads its taps, so weighted pairs always clamp);
 // otherwise every slice takes the view with weight 1.
-template <int PITCH, int MODE, bool WEIGHTED, bool CLAMP>
+// T: the thread's slices (T / 2 pairs).  SOFF > 0: a second set of T slices one pitch up (accumulators
+// accB) reads the same taps, positions and weights from the window SOFF floats further on (a
+// compile-time offset, so its loads reuse the first set's addresses): the slice one pitch up sees the
+// view one turn later exactly as this slice sees this view (Sec. II periodicity).
+template <int PITCH, int MODE, bool WEIGHTED, bool CLAMP, int T = B2_T, int SOFF = 0>
 __device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
-                                        float inv_v, float kf, const float *lo, const float *hi, float2 *acc2)
+                                        float inv_v, float kf, const float *lo, const float *hi, float2 *acc2,
+                                        float2 *accB = nullptr)
 {
     const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
     const __half2 fch = __float2half2_rn(fc);
 #pragma unroll
-    for (int pr = 0; pr < B2_T / 2; ++pr) {
+    for (int pr = 0; pr < T / 2; ++pr) {
         const float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
         if (WEIGHTED) {
             const float2 om = __fmul2_rn(make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1])),
                                          make_float2(__saturatef(hi[2 * pr] - kf), __saturatef(hi[2 * pr + 1] - kf)));
             if (om.x == 0.0f && om.y == 0.0f) continue;
-            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, __fmul2_rn(om, make_float2(inv_v, inv_v)),
-                                       acc2[pr]);
+            const float2 w2 = __fmul2_rn(om, make_float2(inv_v, inv_v));
+            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, w2, acc2[pr]);
+            if (SOFF) bp_tap2<PITCH, MODE, true>(smem + SOFF, colx, fc2, fch, ur2, rmax, w2, accB[pr]);
         } else {
             bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), acc2[pr]);
+            if (SOFF) bp_tap2<PITCH, MODE, CLAMP>(smem + SOFF, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), accB[pr]);
         }
     }
 }
@@ -386,17 +393,17 @@ __device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float 
 // loop stops at the first pair outside; in a boundary pair the closed slice reads
 // its partner's rows (its weight is 0), so the rows stay inside the staged window
 // without clamping.  The weights and taps equal the general weighted path's.
-template <int PITCH, int MODE, bool IN, bool CLAMP>
+template <int PITCH, int MODE, bool IN, bool CLAMP, int T = B2_T, int SOFF = 0>
 __device__ __forceinline__ void bp_view_ramp(const float *smem, uint32_t colx, float fc, float ur0, float dur,
                                              float rmax, float inv_v, float kf, const float *lo, const float *hi,
-                                             float2 *acc2)
+                                             float2 *acc2, float2 *accB = nullptr)
 {
     const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
     const float2 iv2 = make_float2(inv_v, inv_v);
     const __half2 fch = __float2half2_rn(fc);
 #pragma unroll
-    for (int i = 0; i < B2_T / 2; ++i) {
-        const int pr = IN ? i : B2_T / 2 - 1 - i;
+    for (int i = 0; i < T / 2; ++i) {
+        const int pr = IN ? i : T / 2 - 1 - i;
         if (IN ? !(kf > lo[2 * pr]) : !(kf < hi[2 * pr + 1])) break;
         float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
         const float2 om = IN ? make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1]))
@@ -405,7 +412,9 @@ __device__ __forceinline__ void bp_view_ramp(const float *smem, uint32_t colx, f
             if (IN && om.y == 0.0f) ur2.y = ur2.x;
             if (!IN && om.x == 0.0f) ur2.x = ur2.y;
         }
-        bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, __fmul2_rn(om, iv2), acc2[pr]);
+        const float2 w2 = __fmul2_rn(om, iv2);
+        bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, w2, acc2[pr]);
+        if (SOFF) bp_tap2<PITCH, MODE, CLAMP>(smem + SOFF, colx, fc2, fch, ur2, rmax, w2, accB[pr]);
     }
 }
 
@@ -416,10 +425,11 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// Geometry of two consecutive views for one voxel column, in FP32x2 with the
-// scalar path's rounding order: column index and fraction of alpha* (the
-// floor taken as 1.5 * 2^23 + floor(c) rounded down), first staged row of
-// slice 0, row step per slice, and 1/v*.
+// Geometry of two consecutive views for one voxel column, in FP32x2, from the tile's reference
+// rays (table rows gA0 gA1 / gB0 gB1 of the two views, cs = (cos, sin) of both): the column index
+// relative to the staged window's first column and its fraction (the floor taken as 1.5 * 2^23 +
+// floor(c) rounded down), first staged row of slice 0, row step per slice, and 1/v*.  (ox, oy): the
+// voxel's offset from its tile centre.
 struct ViewGeo2 {
     float2 fc, ur0, dur, inv_v;
     int ci0, ci1;
@@ -427,32 +437,30 @@ struct ViewGeo2 {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-template <bool POLY>
-__device__ __forceinline__ void view_geo2(const BPArgs &a, float x, float y, float2 csA, float2 csB, float zb,
-                                          float zb_lo, float kfA, ViewGeo2 &g)
+__device__ __forceinline__ void view_geo2(const BPArgs &a, float ox, float oy, float4 cs, float4 gA0, float4 gA1,
+                                          float4 gB0, float4 gB1, float zb, float zb_lo, float kfA, ViewGeo2 &g)
 {
     const float2 m1 = f2(-1.0f);
-    const float2 cx = make_float2(csA.x, csB.x), cy = make_float2(csA.y, csB.y);
-    const float2 v = __ffma2_rn(f2(-x), cx, __ffma2_rn(f2(-y), cy, f2(a.R)));
-    const float2 u = __ffma2_rn(f2(-x), cy, __fmul2_rn(f2(y), cx));
-    g.inv_v = make_float2(rcp_approx(v.x), rcp_approx(v.y));
-    const float2 t = __fmul2_rn(u, g.inv_v);
-    float2 ang;
-    if (POLY) {
-        const float2 s2 = __fmul2_rn(t, t);
-        float2 pp = f2(c_atan[0]);
-#pragma unroll
-        for (int i = 1; i < kAtanTerms; ++i) pp = __ffma2_rn(pp, s2, f2(c_atan[i]));
-        ang = __fmul2_rn(__fmul2_rn(t, pp), f2(a.inv_da));
-    } else {
-        ang = make_float2(atanf(t.x) * a.inv_da, atanf(t.y) * a.inv_da);
-    }
-    const float2 c = __fadd2_rn(__fadd2_rn(ang, f2(-a.K_hi)), f2(-a.K_lo));
-    const float2 yv = __fadd2_rd(c, f2(12582912.0f));  // 1.5 * 2^23 + floor(c), |c| < 2^22
+    const float2 c = make_float2(cs.x, cs.z), sn = make_float2(cs.y, cs.w);
+    const float2 ur = make_float2(gA0.x, gB0.x), vr = make_float2(gA0.y, gB0.y);
+    const float2 du = __ffma2_rn(f2(-ox), sn, __ffma2_rn(f2(oy), c, make_float2(gA0.z, gB0.z)));
+    const float2 dv = __ffma2_rn(f2(-ox), c, __ffma2_rn(f2(-oy), sn, make_float2(gA0.w, gB0.w)));
+    const float2 cross = __ffma2_rn(du, vr, __fmul2_rn(dv, __fmul2_rn(ur, m1)));
+    const float2 dot = __ffma2_rn(ur, du, __ffma2_rn(vr, dv, make_float2(gA1.x, gB1.x)));
+    const float2 t = __fmul2_rn(cross, make_float2(rcp_approx(dot.x), rcp_approx(dot.y)));
+    const float2 s2 = __fmul2_rn(t, t);
+    float2 p = __ffma2_rn(s2, f2(-1.0f / 11.0f), f2(1.0f / 9.0f));
+    p = __ffma2_rn(s2, p, f2(-1.0f / 7.0f));
+    p = __ffma2_rn(s2, p, f2(1.0f / 5.0f));
+    p = __ffma2_rn(s2, p, f2(-1.0f / 3.0f));
+    const float2 at = __ffma2_rn(__fmul2_rn(t, s2), p, t);
+    const float2 cr = __fadd2_rn(__ffma2_rn(at, f2(a.inv_da), make_float2(gA1.z, gB1.z)), make_float2(gA1.y, gB1.y));
+    const float2 yv = __fadd2_rd(cr, f2(12582912.0f));  // 1.5 * 2^23 + floor(cr), |cr| < 2^22
     g.ci0 = __float_as_int(yv.x) - 0x4B400000;
     g.ci1 = __float_as_int(yv.y) - 0x4B400000;
-    const float2 cf = __fadd2_rn(yv, f2(-12582912.0f));
-    g.fc = __fadd2_rn(__ffma2_rn(__fadd2_rn(cf, f2(a.K_hi)), m1, ang), f2(-a.K_lo));
+    g.fc = __ffma2_rn(__fadd2_rn(yv, f2(-12582912.0f)), m1, cr);
+    const float2 v = __fadd2_rn(vr, dv), u = __fadd2_rn(ur, du);
+    g.inv_v = make_float2(rcp_approx(v.x), rcp_approx(v.y));
     const float2 M = __fmul2_rn(f2(a.D), make_float2(rsqrtf(fmaf(u.x, u.x, v.x * v.x)), rsqrtf(fmaf(u.y, u.y, v.y * v.y))));
     const float2 kf = make_float2(kfA, kfA + 1.0f);
     const float2 zr = __fadd2_rn(__ffma2_rn(f2(-a.hdl), kf, f2(zb)), __ffma2_rn(f2(-a.hdl_lo), kf, f2(zb_lo)));
@@ -462,14 +470,18 @@ __device__ __forceinline__ void view_geo2(const BPArgs &a, float x, float y, flo
 
 // RANGED: the launch takes a share of the views (BPArgs k_lo .. acc_final); the plain form
 // compiles without that bookkeeping.
-template <int PITCH, int MODE, bool POLY, bool ROWS_OK, bool RANGED, int RP>
+// PARTIAL: the launch's last z tile holds fewer than B2_T slices.  Its missing slices take every view
+// with clamped rows (nothing of them is stored), so the tile keeps the full and ramp paths instead
+// of weighing every view; launched with ROWS_OK false.
+template <int PITCH, int MODE, bool ROWS_OK, bool RANGED, int RP, bool PARTIAL = false>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_tma(const __grid_constant__ CUtensorMap gmap, BP2Args p)
 {
+    static_assert(!PARTIAL || !ROWS_OK, "a partial tile's missing slices read clamped rows");
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
-    __shared__ int2 s_col[RP];     // first window column of the pair's two views
-    __shared__ float4 s_cs[RP];    // (cos, sin) of the pair's two views
+    __shared__ float4 s_geo[RP][4];  // the pair's two views' table rows (tile reference rays, window start)
+    __shared__ float4 s_cs[RP];      // (cos, sin) of the pair's two views
     __shared__ int s_K0, s_K1;
     const BPArgs &a = p.a;
     const int tid = threadIdx.x;
@@ -505,8 +517,10 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 kmin = min(kmin, ka[t]);
                 kmax = max(kmax, kb[t]);
             }
-            kfull_lo = max(kfull_lo, ka[t]);
-            kfull_hi = min(kfull_hi, kb[t]);
+            if (!(PARTIAL && active && s >= a.s_end)) {
+                kfull_lo = max(kfull_lo, ka[t]);
+                kfull_hi = min(kfull_hi, kb[t]);
+            }
         }
         if (!p.mono) {  // windows not monotone in the slice: no full range and no ramp walk
             kfull_lo = INT32_MAX;
@@ -520,6 +534,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             if (ka[t] <= kb[t]) {
                 lo[t] = (float)(ka[t] - kbase) - wa[t];
                 hi[t] = (float)(kb[t] - kbase) + wb[t];
+            } else if (PARTIAL && active) {  // a missing slice of a partial tile: open in every view
+                lo[t] = -3.0e9f;
+                hi[t] = 3.0e9f;
             } else {
                 lo[t] = 3.0e9f;
                 hi[t] = -3.0e9f;
@@ -561,49 +578,50 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     }
 
     if (producer) {
-        // ---------------- producer warp: column window + TMA for each view
-        const int ixa = blockIdx.x * B2_TX, iya = blockIdx.y * B2_TY;
-        // tile corners (voxel centres inside the volume): alpha* over the tile
-        // is extremal at them (u*/v* is linear-fractional in (x, y))
-        const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
-        const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
+        // ---------------- producer warp: the views' table rows (window start in them) + TMA
+        const float4 *geo_t = p.geo + (size_t)(blockIdx.y * p.geo_ntx + blockIdx.x) * a.vpt * 2;
         const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
         const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
         int ps = 0, issued = 0;  // pair slot; view pairs issued
         uint32_t phase = 0;
         int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
         bool ok = true;
+        // the next pair's table rows (tile reference rays, window start) and (cos, sin), loaded a pair
+        // ahead of their use so that their latency overlaps the wait for a free slot
+        float4 gA0, gA1, gB0, gB1;
+        float2 csA, csB;
+        auto load_rows = [&](int km) {
+            const int km1 = km + 1 == a.vpt ? 0 : km + 1;
+            gA0 = __ldg(geo_t + 2 * km);
+            gA1 = __ldg(geo_t + 2 * km + 1);
+            gB0 = __ldg(geo_t + 2 * km1);
+            gB1 = __ldg(geo_t + 2 * km1 + 1);
+            csA = __ldg(a.trig + km);
+            csB = __ldg(a.trig + km1);
+        };
+        if (lane == 0) load_rows(kmod);
         for (int j = 0; j < nviews; j += 2) {
 #ifdef KATS_DEBUG_CHECKS
             if (g_debug_stall_pairs >= 0 && j / 2 >= g_debug_stall_pairs) break;  // test hook: stop issuing
 #endif
+            const int kmod1 = kmod + 1 == a.vpt ? 0 : kmod + 1;
             if (j >= 2 * RP && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
                 ok = false;
                 break;
             }
             const int nv2 = min(2, nviews - j);
-            const int kmod1 = kmod + 1 == a.vpt ? 0 : kmod + 1;
-            const float2 csA = __ldg(a.trig + kmod), csB = __ldg(a.trig + kmod1);
-            int clo[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 cs = h ? csB : csA;
-                const float v = a.R - cx * cs.x - cy * cs.y;
-                const float u = -cx * cs.y + cy * cs.x;
-                float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
-                c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
-                c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
-                // one column of slack left of the lowest tap, start aligned to 4 floats (16 bytes)
-                clo[h] = ((int)floorf(c) - 1) & ~3;
-            }
             if (lane == 0) {
-                s_col[ps] = make_int2(clo[0], clo[1]);
+                s_geo[ps][0] = gA0;
+                s_geo[ps][1] = gA1;
+                s_geo[ps][2] = gB0;
+                s_geo[ps][3] = gB1;
                 s_cs[ps] = make_float4(csA.x, csA.y, csB.x, csB.y);
                 mbar_arrive_expect_tx(&s_full[ps], box_bytes * (uint32_t)nv2);
                 // fp32 windows start one zero row above the detector; row-pair windows at pair-row 0
                 for (int h = 0; h < nv2; ++h)
-                    tma_load_3d(dst0 + 4u * (uint32_t)((2 * ps + h) * p.slot_floats), &gmap, &s_full[ps], clo[h],
-                                MODE == 0 ? -1 : 0, K0 + j + h - (int)a.first_view);
+                    tma_load_3d(dst0 + 4u * (uint32_t)((2 * ps + h) * p.slot_floats), &gmap, &s_full[ps],
+                                __float_as_int(h ? gB1.w : gA1.w), MODE == 0 ? -1 : 0, K0 + j + h - (int)a.first_view);
+                if (j + 2 < nviews) load_rows(kmod1 + 1 == a.vpt ? 0 : kmod1 + 1);
             }
             __syncwarp();
             issued = j / 2 + 1;
@@ -627,8 +645,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     }
 
     // ---------------- consumer warps: two views per iteration, their per-view
-    // geometry computed together in FP32x2
-    const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
+    // geometry computed together in FP32x2 (offset from the tile centre, exact)
+    const float ox = ((float)tx - 0.5f * (B2_TX - 1)) * a.dx, oy = ((float)ty - 0.5f * (B2_TY - 1)) * a.dy;
     const int kbase = active ? kmin : 0;
     float zb, zb_lo;
     z_base(a, s0, kbase, &zb, &zb_lo);
@@ -649,19 +667,16 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         if (onA || onB) {
             const float kfA = (float)(kA - kbase);
             ViewGeo2 g;
-            const float4 cs4 = s_cs[ps];
-            const int2 col2 = s_col[ps];
-            view_geo2<POLY>(a, x, y, make_float2(cs4.x, cs4.y), make_float2(cs4.z, cs4.w), zb, zb_lo, kfA, g);
+            view_geo2(a, ox, oy, s_cs[ps], s_geo[ps][0], s_geo[ps][1], s_geo[ps][2], s_geo[ps][3], zb, zb_lo, kfA, g);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!(h ? onB : onA)) continue;
-                const int k = kA + h, sl = 2 * ps + h, col0 = h ? col2.y : col2.x;
+                const int k = kA + h, sl = 2 * ps + h;
                 const float fc = h ? g.fc.y : g.fc.x, ur0 = h ? g.ur0.y : g.ur0.x, dur = h ? g.dur.y : g.dur.x;
                 const float inv_v = h ? g.inv_v.y : g.inv_v.x, kf = kfA + (float)h;
-                KATS_DCHECK((h ? g.ci1 : g.ci0) - col0 >= 0 && (h ? g.ci1 : g.ci0) - col0 <= p.W - 2, 1);
-                const uint32_t colx =
-                    (uint32_t)(base + sl * p.slot_floats + min(max((h ? g.ci1 : g.ci0) - col0, 0), p.W - 2)) -
-                    (0x4B000000u << SH);
+                KATS_DCHECK((h ? g.ci1 : g.ci0) >= 0 && (h ? g.ci1 : g.ci0) <= p.W - 2, 1);
+                const uint32_t colx = (uint32_t)(base + sl * p.slot_floats + min(max(h ? g.ci1 : g.ci0, 0), p.W - 2)) -
+                                      (0x4B000000u << SH);
                 // full: every slice inside its window with weight 1; ramps: windows
                 // still opening (no slice ended) or closing (every slice started); a plan
                 // without monotone windows has an empty full range (every view general)
@@ -691,6 +706,232 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             const float v = (t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x;
             a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = (!RANGED || a.acc_final) ? v * p.out_scale : v;
         }
+    }
+}
+
+// Geometry of one view for one voxel column (the scalar form of view_geo2).
+struct ViewGeo1 {
+    float fc, ur0, dur, inv_v;
+    int ci;
+};
+
+__device__ __forceinline__ void view_geo1(const BPArgs &a, float ox, float oy, float2 cs, float4 g0, float4 g1,
+                                          float zb, float zb_lo, float kf, ViewGeo1 &g)
+{
+    const float du = fmaf(-ox, cs.y, fmaf(oy, cs.x, g0.z));
+    const float dv = fmaf(-ox, cs.x, fmaf(-oy, cs.y, g0.w));
+    const float cross = fmaf(du, g0.y, dv * -g0.x);
+    const float dot = fmaf(g0.x, du, fmaf(g0.y, dv, g1.x));
+    const float cr = fmaf(atan_small(cross * rcp_approx(dot)), a.inv_da, g1.z) + g1.y;
+    const float yv = __fadd_rd(cr, 12582912.0f);  // 1.5 * 2^23 + floor(cr)
+    g.ci = __float_as_int(yv) - 0x4B400000;
+    g.fc = cr - (yv - 12582912.0f);
+    const float v = g0.y + dv, u = g0.x + du;
+    g.inv_v = rcp_approx(v);
+    const float M = a.D * rsqrtf(fmaf(u, u, v * v));
+    const float zr = fmaf(-a.hdl, kf, zb) + fmaf(-a.hdl_lo, kf, zb_lo);
+    g.ur0 = fmaf(fmaf(M, zr, -a.w0row), a.inv_dw, 1.0f);  // staged row 0 = detector row -1
+    g.dur = M * a.dz_over_dw;
+}
+
+// Work items of a paired launch: A slices [s0, s0 + T) and B slices [s0 + N, s0 + N + T).
+constexpr int kMaxPairItems = 64;
+struct PairItems {
+    int n;
+    int s0[kMaxPairItems];
+};
+
+// Paired-pitch backprojection.  A CTA owns B2_TX x B2_TY columns and two groups of T slices one pitch
+// apart (A at s0, B at s0 + N).  By the periodicity of Sec. II a B slice's PI window is its A
+// slice's one turn later, and at view k + views_per_turn it sees the same alpha*, v*, w* as the A
+// slice at view k; so a thread computes each view's geometry, window classification and end
+// weights once for both groups, and only the taps differ: the producer stages view k (for A) and
+// view k + views_per_turn (for B) with the same column window into a slot pair, one view per
+// consumer iteration.  Ring of RP slot pairs; everything else as k_backproject_tma.
+// Staged rows a paired slot holds (fp32: n_rows + 3, row pairs: n_rows + 2): the slots have a fixed
+// size of PITCH x kPairRows floats, so the B window's offset is a compile-time constant.
+constexpr int kPairRows = 72;
+
+template <int PITCH, int MODE, bool ROWS_OK, int T, int RP>
+__global__ void __launch_bounds__(B2_THREADS, 2)
+    k_backproject_pair(const __grid_constant__ CUtensorMap gmap, BP2Args p, const __grid_constant__ PairItems it)
+{
+    constexpr int SLOT = PITCH * kPairRows;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
+    __shared__ float4 s_geo[RP][2];  // the view's table rows (tile reference ray, window start)
+    __shared__ float2 s_cs[RP];      // its (cos, sin)
+    __shared__ int s_K0, s_K1;
+    const BPArgs &a = p.a;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool producer = warp == B2_CW;
+    const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
+    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    const int s0 = it.s0[blockIdx.z];
+    const bool active = !producer && ix < a.nx && iy < a.ny;
+    const int base = (int)(((128u - (smem_addr(smem) & 127u)) & 127u) >> 2);
+
+    // per-slice view windows of the A group (the B group's are one turn later)
+    int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
+    float lo[T], hi[T];
+    float2 accA[T / 2], accB[T / 2];
+    {
+        int ka[T], kb[T];
+        float wa[T], wb[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int s = s0 + t;
+            ka[t] = INT32_MAX;
+            kb[t] = INT32_MIN;
+            wa[t] = wb[t] = 0.0f;
+            if (active) {
+                const int j = s % a.N, m = s / a.N;
+                const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
+                ka[t] = a.k0[o] + m * a.vpt;
+                kb[t] = a.k1[o] + m * a.vpt;
+                wa[t] = a.w0[o];
+                wb[t] = a.w1[o];
+                kmin = min(kmin, ka[t]);
+                kmax = max(kmax, kb[t]);
+            }
+            kfull_lo = max(kfull_lo, ka[t]);
+            kfull_hi = min(kfull_hi, kb[t]);
+        }
+        if (!p.mono) {
+            kfull_lo = INT32_MAX;
+            kfull_hi = INT32_MIN;
+        }
+        const int kbase = active ? kmin : 0;
+#pragma unroll
+        for (int t = 0; t < T / 2; ++t) accA[t] = accB[t] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            lo[t] = (float)(ka[t] - kbase) - wa[t];
+            hi[t] = (float)(kb[t] - kbase) + wb[t];
+        }
+    }
+    if (tid == 0) {
+        s_K0 = INT32_MAX;
+        s_K1 = INT32_MIN;
+        for (int r = 0; r < RP; ++r) {
+            mbar_init(&s_full[r], 1);
+            mbar_init(&s_empty[r], B2_CW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (active) {
+        atomicMin(&s_K0, kmin);
+        atomicMax(&s_K1, kmax);
+    }
+    __syncthreads();
+    const int K0 = s_K0, K1 = s_K1;
+    if (K0 > K1) return;  // uniform: no column of the tile in the volume
+    const int nviews = K1 - K0 + 1;
+
+    if (producer) {
+        const float4 *geo_t = p.geo + (size_t)(blockIdx.y * p.geo_ntx + blockIdx.x) * a.vpt * 2;
+        const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
+        const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
+        int ps = 0, issued = 0;
+        uint32_t phase = 0;
+        int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
+        bool ok = true;
+        float4 g0, g1;
+        float2 cs;
+        if (lane == 0) {
+            g0 = __ldg(geo_t + 2 * kmod);
+            g1 = __ldg(geo_t + 2 * kmod + 1);
+            cs = __ldg(a.trig + kmod);
+        }
+        for (int j = 0; j < nviews; ++j) {
+#ifdef KATS_DEBUG_CHECKS
+            if (g_debug_stall_pairs >= 0 && j >= g_debug_stall_pairs) break;  // test hook: stop issuing
+#endif
+            if (j >= RP && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
+                ok = false;
+                break;
+            }
+            if (lane == 0) {
+                s_geo[ps][0] = g0;
+                s_geo[ps][1] = g1;
+                s_cs[ps] = cs;
+                mbar_arrive_expect_tx(&s_full[ps], 2 * box_bytes);
+                const int clo = __float_as_int(g1.w), kv = K0 + j - (int)a.first_view;
+                tma_load_3d(dst0 + 4u * (uint32_t)(2 * ps * SLOT), &gmap, &s_full[ps], clo, MODE == 0 ? -1 : 0, kv);
+                tma_load_3d(dst0 + 4u * (uint32_t)((2 * ps + 1) * SLOT), &gmap, &s_full[ps], clo, MODE == 0 ? -1 : 0,
+                            kv + a.vpt);
+                kmod = kmod + 1 == a.vpt ? 0 : kmod + 1;
+                if (j + 1 < nviews) {
+                    g0 = __ldg(geo_t + 2 * kmod);
+                    g1 = __ldg(geo_t + 2 * kmod + 1);
+                    cs = __ldg(a.trig + kmod);
+                }
+            }
+            __syncwarp();
+            issued = j + 1;
+            if (++ps == RP) {
+                ps = 0;
+                phase ^= 1u;
+            }
+        }
+        if (lane == 0) {
+            bool landed = true;
+            for (int i = max(0, issued - RP); i < issued; ++i)
+                landed = mbar_wait(&s_full[i % RP], (uint32_t)((i / RP) & 1)) && landed;
+            if (!ok || !landed) atomicExch(p.status, kDevStatusTimeout);
+        }
+        return;
+    }
+
+    const float ox = ((float)tx - 0.5f * (B2_TX - 1)) * a.dx, oy = ((float)ty - 0.5f * (B2_TY - 1)) * a.dy;
+    const int kbase = active ? kmin : 0;
+    float zb, zb_lo;
+    z_base(a, s0, kbase, &zb, &zb_lo);
+    const float rmax = (float)(a.n_rows + 1);
+    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
+    int ps = 0;
+    uint32_t phase = 0;
+    for (int j = 0; j < nviews; ++j) {
+        const int k = K0 + j;
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_full[ps], phase))) {
+            if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
+            return;
+        }
+        if (active && k >= kmin && k <= kmax) {
+            const float kf = (float)(k - kbase);
+            ViewGeo1 g;
+            view_geo1(a, ox, oy, s_cs[ps], s_geo[ps][0], s_geo[ps][1], zb, zb_lo, kf, g);
+            KATS_DCHECK(g.ci >= 0 && g.ci <= p.W - 2, 1);
+            const uint32_t colx = (uint32_t)(base + 2 * ps * SLOT + min(max(g.ci, 0), p.W - 2)) - (0x4B000000u << SH);
+            if (k > kfull_lo && k < kfull_hi)
+                bp_view<PITCH, MODE, false, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf, lo,
+                                                               hi, accA, accB);
+            else if (k < kfull_hi)
+                bp_view_ramp<PITCH, MODE, true, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf,
+                                                                   lo, hi, accA, accB);
+            else if (k > kfull_lo)
+                bp_view_ramp<PITCH, MODE, false, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf,
+                                                                    lo, hi, accA, accB);
+            else
+                bp_view<PITCH, MODE, true, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf, lo,
+                                                              hi, accA, accB);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[ps]);
+        if (++ps == RP) {
+            ps = 0;
+            phase ^= 1u;
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const float va = (t & 1) ? accA[t >> 1].y : accA[t >> 1].x;
+        const float vb = (t & 1) ? accB[t >> 1].y : accB[t >> 1].x;
+        a.vol[((int64_t)(s0 + t) * a.ny + iy) * a.nx + ix] = va * p.out_scale;
+        a.vol[((int64_t)(s0 + a.N + t) * a.ny + iy) * a.nx + ix] = vb * p.out_scale;
     }
 }
 
@@ -787,17 +1028,55 @@ static int window_cols(const Plan &p)
     return ((int)ceil(span) + 8 + 3) / 4 * 4;
 }
 
-template <int PITCH, int MODE, int RP>
-static auto select_tma(bool ranged, bool poly, bool rows_ok)
+// Decomposition of slices [S0, S1) for the paired kernel: from S0 on, blocks of 2N slices whose
+// first N pair with the next N; each block's pairs [a, a + L) go in items of T slices (T of the
+// instantiated 12, 14 leaving the fewest slices unpaired, the larger on a tie), the rest are
+// ranges for the single kernel.  False when the launch holds no full item.
+struct PairPlan {
+    int T = 0;
+    std::vector<int> items;                  // first A slice of each item
+    std::vector<std::pair<int, int>> rest;  // unpaired slice ranges [s, e)
+};
+
+static bool pair_plan(int S0, int S1, int N, PairPlan *out)
 {
-    return ranged ? (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, true, RP>
-                                     : k_backproject_tma<PITCH, MODE, true, false, true, RP>)
-                          : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, true, RP>
-                                     : k_backproject_tma<PITCH, MODE, false, false, true, RP>))
-                  : (poly ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, false, RP>
-                                     : k_backproject_tma<PITCH, MODE, true, false, false, RP>)
-                          : (rows_ok ? k_backproject_tma<PITCH, MODE, false, true, false, RP>
-                                     : k_backproject_tma<PITCH, MODE, false, false, false, RP>));
+    PairPlan best;
+    int best_rest = INT32_MAX;
+    for (int T : {14, 12}) {
+        PairPlan pp;
+        pp.T = T;
+        int a0 = S0, n_rest = 0;
+        auto add_rest = [&](int s, int e) {
+            if (e <= s) return;
+            if (!pp.rest.empty() && pp.rest.back().second == s)
+                pp.rest.back().second = e;
+            else
+                pp.rest.push_back({s, e});
+            n_rest += e - s;
+        };
+        for (; a0 + N < S1; a0 += 2 * N) {
+            const int L = std::min(N, S1 - a0 - N), nfull = L / T;
+            for (int i = 0; i < nfull; ++i) pp.items.push_back(a0 + i * T);
+            add_rest(a0 + nfull * T, a0 + N);
+            add_rest(a0 + N + nfull * T, std::min(a0 + 2 * N, S1));
+        }
+        add_rest(a0, S1);
+        if (!pp.items.empty() && n_rest < best_rest) {
+            best_rest = n_rest;
+            best = pp;
+        }
+    }
+    if (best.items.empty()) return false;
+    *out = best;
+    return true;
+}
+
+template <int PITCH, int MODE, int RP>
+static auto select_tma(bool ranged, bool rows_ok)
+{
+    return ranged ? (rows_ok ? k_backproject_tma<PITCH, MODE, true, true, RP> : k_backproject_tma<PITCH, MODE, false, true, RP>)
+                  : (rows_ok ? k_backproject_tma<PITCH, MODE, true, false, RP>
+                             : k_backproject_tma<PITCH, MODE, false, false, RP>);
 }
 
 template <int PITCH, int MODE>
@@ -815,7 +1094,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     const size_t smem = ring_bytes(rp);
     EncodeTiledFn enc = encode_fn();
     if (!enc || W > PITCH || PITCH > p.gf_cols || srows > 256 || smem > kMax ||
-        (reinterpret_cast<uintptr_t>(gF) % 16) != 0 || p.n_fviews >= INT32_MAX)
+        (reinterpret_cast<uintptr_t>(gF) % 16) != 0 || p.n_fviews >= INT32_MAX || !(p.geo_tmax <= kTileTanMax))
         return KATS_OK;
     const int64_t drows = p.g.n_rows + (MODE == 0 ? 0 : 1);
     CUtensorMap map;
@@ -828,22 +1107,66 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return KATS_OK;
     BP2Args b{a, W, srows, slot, p.dev_status, (float)(p.dlam / (2.0 * kPi) / (MODE == 0 ? 1.0 : p.g.d_alpha)),
-              p.pi_monotone && !g_debug_nonmono.load() ? 1 : 0};
-    // |u*/v*| <= r_fov / sqrt(R^2 - r_fov^2) <= 1 lets the polynomial arctan skip range reduction
-    const bool poly = p.r_fov <= p.g.R * 0.70710678;
+              p.pi_monotone && !g_debug_nonmono.load() ? 1 : 0, p.geo, p.geo_ntx};
     // every contributing row within half a row of the detector (plan extents, FP32 on device)
     const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
     const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
     const bool ranged = a.k_lo != INT32_MIN || a.k_hi != INT32_MAX || a.acc_in || !a.acc_final;
-    auto kern = rp == 3 ? select_tma<PITCH, MODE, 3>(ranged, poly, rows_ok)
-                        : select_tma<PITCH, MODE, 2>(ranged, poly, rows_ok);
+    auto kern = rp == 3 ? select_tma<PITCH, MODE, 3>(ranged, rows_ok) : select_tma<PITCH, MODE, 2>(ranged, rows_ok);
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
-              (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
-    kern<<<grid, B2_THREADS, smem, st>>>(map, b);
-    count_launches(1);
-    KATS_CUDA(cudaGetLastError());
+    const unsigned gx = (unsigned)ceil_div(p.g.nx, B2_TX), gy = (unsigned)ceil_div(p.g.ny, B2_TY);
+    // slices [s, e) in 16-slice z tiles
+    // slices [s, e) in 16-slice z tiles; without view ranges a last partial tile goes to the PARTIAL form
+    auto single = [&](int s, int e) -> int {
+        if (e <= s) return KATS_OK;
+        const int e_full = ranged ? e : s + (e - s) / B2_T * B2_T;
+        BP2Args bs = b;
+        if (e_full > s) {
+            bs.a.s_begin = s;
+            bs.a.s_end = e_full;
+            kern<<<dim3(gx, gy, (unsigned)ceil_div(e_full - s, B2_T)), B2_THREADS, smem, st>>>(map, bs);
+            count_launches(1);
+            KATS_CUDA(cudaGetLastError());
+        }
+        if (e_full < e) {
+            auto kp = rp == 3 ? k_backproject_tma<PITCH, MODE, false, false, 3, true>
+                              : k_backproject_tma<PITCH, MODE, false, false, 2, true>;
+            KATS_CUDA(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bs.a.s_begin = e_full;
+            bs.a.s_end = e;
+            kp<<<dim3(gx, gy, 1), B2_THREADS, smem, st>>>(map, bs);
+            count_launches(1);
+            KATS_CUDA(cudaGetLastError());
+        }
+        return KATS_OK;
+    };
+    // Slices one pitch apart share their views' geometry (Sec. II periodicity): where a launch holds
+    // such pairs and takes every view, the paired kernel reconstructs them together, T slices of each
+    // per thread, and the rest go through the single kernel.
+    PairPlan pp;
+    const size_t pair_smem = sizeof(float) * (size_t)PITCH * kPairRows * 2 * 3 + 128;  // 3 slot pairs
+    if (!ranged && PITCH <= 64 && srows <= kPairRows && pair_smem <= kTwoPerSm &&
+        pair_plan(a.s_begin, a.s_end, (int)p.N, &pp)) {
+        auto pk = pp.T == 12 ? (rows_ok ? k_backproject_pair<PITCH, MODE, true, 12, 3> : k_backproject_pair<PITCH, MODE, false, 12, 3>)
+                             : (rows_ok ? k_backproject_pair<PITCH, MODE, true, 14, 3> : k_backproject_pair<PITCH, MODE, false, 14, 3>);
+        KATS_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
+        for (size_t i0 = 0; i0 < pp.items.size(); i0 += kMaxPairItems) {
+            PairItems it;
+            it.n = (int)std::min<size_t>(kMaxPairItems, pp.items.size() - i0);
+            for (int i = 0; i < it.n; ++i) it.s0[i] = pp.items[i0 + (size_t)i];
+            pk<<<dim3(gx, gy, (unsigned)it.n), B2_THREADS, pair_smem, st>>>(map, b, it);
+            count_launches(1);
+            KATS_CUDA(cudaGetLastError());
+        }
+        for (const auto &r : pp.rest) {
+            int rc = single(r.first, r.second);
+            if (rc) return rc;
+        }
+    } else {
+        int rc = single(a.s_begin, a.s_end);
+        if (rc) return rc;
+    }
     *launched = true;
     return KATS_OK;
 }
@@ -1007,10 +1330,10 @@ constexpr int BT_THREADS = B2_TX * B2_TY;
 // x (already scaled: at most K taps of magnitude below 2^(30 - hb)) into the window at p.
 __device__ __forceinline__ void deposit(int *p, float x) { atomicAdd(p, __float2int_rn(x)); }
 
-template <int PITCH, bool POLY, bool ROWS_OK>
+template <int PITCH, bool ROWS_OK>
 __global__ void __launch_bounds__(BT_THREADS, 2)
     k_backproject_T_win(BPArgs a, int W, int srows, int slot_floats, float out_scale, float inv_v_max, int hb,
-                        int G, const float *__restrict__ vol, float *gF)
+                        int G, const float4 *__restrict__ geo, int geo_ntx, const float *__restrict__ vol, float *gF)
 {
     constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
     extern __shared__ int win[];  // [2 windows][G copies][slot_floats] fixed-point sums
@@ -1095,19 +1418,12 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     if (K0 > K1) return;  // uniform: no voxel of the tile has a PI view
     const int nviews = K1 - K0 + 1;
 
-    // first window column of view k: lowest column touched at the tile corners, one column of slack
-    const int ixa = blockIdx.x * B2_TX, iya = blockIdx.y * B2_TY;
-    const float cx = a.x0 + (float)((lane & 1) ? min(ixa + B2_TX - 1, a.nx - 1) : ixa) * a.dx;
-    const float cy = a.y0 + (float)((lane & 2) ? min(iya + B2_TY - 1, a.ny - 1) : iya) * a.dy;
+    // first window column of view k: the plan's table (lowest column touched at the tile corners,
+    // one column of slack, 16-byte aligned)
+    const float4 *geo_t = geo + (size_t)(blockIdx.y * geo_ntx + blockIdx.x) * a.vpt * 2;
     auto window_col = [&](int k) {
         const int km = ((k % a.vpt) + a.vpt) % a.vpt;
-        const float2 cs = __ldg(a.trig + km);
-        const float v = a.R - cx * cs.x - cy * cs.y;
-        const float u = -cx * cs.y + cy * cs.x;
-        float c = angle_cols<POLY>(a, u * (1.0f / v)) - a.K_hi;
-        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 1));
-        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, 2));
-        return ((int)floorf(c) - 1) & ~3;
+        return __float_as_int(__ldg(geo_t + 2 * km + 1).w);
     };
     if (warp == 0) {
         const int c = window_col(K0);
@@ -1115,7 +1431,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     }
     __syncthreads();
 
-    const float x = a.x0 + (float)ix * a.dx, y = a.y0 + (float)iy * a.dy;
+    const float ox = ((float)tx - 0.5f * (B2_TX - 1)) * a.dx, oy = ((float)ty - 0.5f * (B2_TY - 1)) * a.dy;
     const int kbase = kmin <= kmax ? kmin : 0;
     float zb, zb_lo;
     z_base(a, s0, kbase, &zb, &zb_lo);
@@ -1138,16 +1454,21 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
         }
         int r_first = INT32_MAX, r_last = -1;  // staged rows this thread deposits into in view k
         if (active && k >= kmin && k <= kmax) {
+            // the voxel's ray against its tile centre's (the forward kernel's tile-relative geometry)
             const float2 cs = __ldg(a.trig + km);
-            const float v = fmaf(-x, cs.x, fmaf(-y, cs.y, a.R));
-            const float u = fmaf(-x, cs.y, y * cs.x);
+            const float4 g0 = __ldg(geo_t + 2 * km), g1 = __ldg(geo_t + 2 * km + 1);
+            const float du = fmaf(-ox, cs.y, fmaf(oy, cs.x, g0.z));
+            const float dv = fmaf(-ox, cs.x, fmaf(-oy, cs.y, g0.w));
+            const float cross = fmaf(du, g0.y, dv * -g0.x);
+            const float dot = fmaf(g0.x, du, fmaf(g0.y, dv, g1.x));
+            const float cr = fmaf(atan_small(cross * rcp_approx(dot)), a.inv_da, g1.z) + g1.y;
+            const float yv = __fadd_rd(cr, 12582912.0f);  // 1.5 * 2^23 + floor(cr)
+            const int ci = __float_as_int(yv) - 0x4B400000;
+            const float fc = cr - (yv - 12582912.0f);
+            const float v = g0.y + dv, u = g0.x + du;
             const float inv_v = rcp_approx(v);
-            int ci;
-            float fc;
-            column_split(a, angle_cols<POLY>(a, u * inv_v), &ci, &fc);
-            KATS_DCHECK(ci - s_col[j % 3] >= 0 && ci - s_col[j % 3] <= W - 2, 4);
-            const uint32_t colx = (uint32_t)((b * G + (warp & (G - 1))) * slot_floats +
-                                             min(max(ci - s_col[j % 3], 0), W - 2)) -
+            KATS_DCHECK(ci >= 0 && ci <= W - 2, 4);
+            const uint32_t colx = (uint32_t)((b * G + (warp & (G - 1))) * slot_floats + min(max(ci, 0), W - 2)) -
                                   (0x4B000000u << SH);
             const float M = a.D * rsqrtf(fmaf(u, u, v * v));
             const float kf = (float)(k - kbase);
@@ -1265,19 +1586,18 @@ static int launch_adjoint_win(const Plan &p, const BPArgs &a, const float *vol, 
     const double taps = 2.0 * (std::floor(1.0 / dur_min) + 1.0);
     const int hb = (int)std::ceil(std::log2((double)(BT_THREADS / G) * taps));
     if (hb > 24) return KATS_OK;  // quantum coarser than 2^-6 c_max: leave it to the global-atomic kernel
-    const bool poly = p.r_fov <= p.g.R * 0.70710678;
+    if (!(p.geo_tmax <= kTileTanMax)) return KATS_OK;
     const double w_first = -0.5 * (double)(p.g.n_rows - 1) * p.g.d_w + p.g.w_offset;
     const double w_last = w_first + (double)(p.g.n_rows - 1) * p.g.d_w;
     const bool rows_ok = p.ext[4] >= w_first - 0.5 * p.g.d_w && p.ext[5] <= w_last + 0.5 * p.g.d_w;
-    auto kern = poly ? (rows_ok ? k_backproject_T_win<PITCH, true, true> : k_backproject_T_win<PITCH, true, false>)
-                     : (rows_ok ? k_backproject_T_win<PITCH, false, true> : k_backproject_T_win<PITCH, false, false>);
+    auto kern = rows_ok ? k_backproject_T_win<PITCH, true> : k_backproject_T_win<PITCH, false>;
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)ceil_div(p.g.nx, B2_TX), (unsigned)ceil_div(p.g.ny, B2_TY),
               (unsigned)ceil_div(a.s_end - a.s_begin, B2_T));
     // 1/v* <= 1/(R - r_fov) for every voxel column, rounded up
     const float inv_v_max = (float)(1.0 / (p.g.R - p.r_fov)) * 1.0001f;
-    kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, hb, G, vol,
-                                         gF);
+    kern<<<grid, BT_THREADS, smem, st>>>(a, W, srows, slot, (float)(p.dlam / (2.0 * kPi)), inv_v_max, hb, G, p.geo,
+                                         p.geo_ntx, vol, gF);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
     *launched = true;

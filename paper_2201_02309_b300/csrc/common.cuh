@@ -16,10 +16,14 @@ namespace kats {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
+// Voxel-column tile of the staged backprojection and its transpose (one thread per column).
+constexpr int kTileX = 16, kTileY = 16;
+
 // Device-resident plan: the pre-calculated tables of one pitch (Sec. II).
 struct Plan {
     kats_geometry g;
     int device;
+    int sm_count = 148;  // multiprocessors of the plan's device
     // derived scalars (FP64, host)
     int64_t N;        // slices per pitch
     int64_t n_psi;    // kappa lines
@@ -59,6 +63,15 @@ struct Plan {
     float2 *trig = nullptr; // [views_per_turn] (cos, sin) of l_{k+1/2} + lambda0, k mod views_per_turn
     float2 *trig_lo = nullptr;  // their rounding residuals: (cos - float(cos), sin - float(sin))
     int *dev_status = nullptr;  // device error word (bounded waits that gave up), 0 = ok
+    // Tile-relative projection (staged backprojection and its transpose): for each kTileX x kTileY
+    // column tile t and view k of a turn, [t][k][2] float4 {u_r, v_r, e_u, e_v}, {r2, c_hi, c_lo, clo}:
+    // the tile centre's u*, v* (FP64) as floats u_r, v_r plus residuals e_u, e_v; r2 = u_r^2 + v_r^2;
+    // the window's first column clo (int bits) and the column coordinate of the ray through (u_r, v_r)
+    // relative to it, c_hi + c_lo.  A voxel's column is then c_hi + c_lo + atan(cross / dot) / d_alpha
+    // with cross, dot formed from its small offset from the centre, with no cancellation.
+    float4 *geo = nullptr;
+    int geo_ntx = 0, geo_nty = 0;
+    float geo_tmax = 0.0f;  // largest |tan| of a voxel's angle from its tile centre's ray
     size_t plan_bytes = 0;
 };
 
@@ -123,6 +136,9 @@ int launch_backproject_adjoint(const Plan &p, const float *vol, float *gF, cudaS
 int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes,
                           cudaStream_t st);
 size_t filter_workspace_bytes(const Plan &p);
+// views per chunk of the filter (steps 1-6 run chunk by chunk through one reused scratch buffer)
+// for a chunk scratch of bytes_per_view per view
+int64_t filter_chunk_views(const Plan &p, size_t bytes_per_view);
 // tensor-core Hilbert step (hilbert_tc.cu); *done = false when it cannot run
 int launch_hilbert_tc(const Plan &p, const float *g3, float *g4, int64_t M, int ldc, cudaStream_t st, bool *done);
 // C[M][ldc] = A[M][K] . B on the tensor cores (3xTF32), B given as hi / lo [N][K] row-major, K a multiple

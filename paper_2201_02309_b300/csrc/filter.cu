@@ -18,11 +18,36 @@ namespace kats {
 // tensor-core K block, zero tail).
 static inline int64_t kpad(const Plan &p) { return p.tc_k; }
 
-// g4 rows are padded to tc_n (whole tensor-core N tiles).
+// Steps 1-6 run chunk by chunk over the filtered views through one reused buffer of a chunk's
+// rebinned data (g3) and Hilbert output (g4), so the workspace holds one chunk of them rather than
+// every view's.  A chunk's g3 + g4 take at most kChunkBudget bytes (about 600 views of the clinical
+// detector: 9 chunks per volume; 128 MiB chunks, 36 per volume, measured 1.3 ms slower per volume
+// from the extra kernel boundaries), and among the lengths that fit, the chunk is the one whose
+// tensor-core tiles best fill whole waves of the SMs.
+int64_t filter_chunk_views(const Plan &p, size_t bytes_per_view)
+{
+    constexpr size_t kChunkBudget = (size_t)480 << 20;
+    const int64_t vmax = std::max<int64_t>(1, std::min<int64_t>(p.n_fviews, (int64_t)(kChunkBudget / bytes_per_view)));
+    const int64_t n_nt = std::max<int64_t>(1, p.tc_n / 256), sms = std::max(1, p.sm_count);
+    int64_t best = vmax;
+    double best_eff = 0.0;
+    for (int64_t v = vmax; v >= std::max<int64_t>(1, vmax / 2); --v) {
+        const int64_t tiles = ceil_div(v * p.n_psi, 128) * n_nt;
+        const double eff = (double)tiles / (double)(ceil_div(tiles, sms) * sms);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = v;
+        }
+    }
+    return best;
+}
+
+static size_t chunk_bytes_per_view(const Plan &p) { return sizeof(float) * (size_t)(p.n_psi * (kpad(p) + p.tc_n)); }
+
+// g3 [chunk][n_psi][Kp] then g4 [chunk][n_psi][tc_n] (rows padded to tensor-core K and N tiles)
 size_t filter_workspace_bytes(const Plan &p)
 {
-    const int64_t nv = p.n_fviews;
-    return sizeof(float) * (size_t)(nv * p.n_psi * kpad(p) + nv * p.n_psi * p.tc_n);
+    return chunk_bytes_per_view(p) * (size_t)filter_chunk_views(p, chunk_bytes_per_view(p));
 }
 
 // ---------------------------------------------------------------- steps 1-3
@@ -231,18 +256,10 @@ __global__ void __launch_bounds__(256) k_unrebin_cos(const float *__restrict__ g
     }
 }
 
-int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st,
-                  int64_t nv_chunk)
+// Steps 1-6 of views [0, nv) of the given pointers, in one pass (nv at most one chunk).
+static int filter_pass(const Plan &p, const float *sino, float *gF, float *g3, float *g4, int64_t nv, cudaStream_t st)
 {
-    kats::NvtxRange nvtx_range("filter (steps 1-6)");
-    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
     const int64_t Kp = kpad(p), nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
-    if (ws_bytes < filter_workspace_bytes(p)) {
-        set_error("filter workspace too small: %zu < %zu", ws_bytes, filter_workspace_bytes(p));
-        return KATS_ESPACE;
-    }
-    float *g3 = (float *)ws;
-    float *g4 = g3 + p.n_fviews * np * Kp;  // workspace laid out for every view; a chunk uses the front
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     // Table entries stay in shared memory while that leaves room for several blocks per SM.
     constexpr size_t kCacheMax = 64 * 1024;
@@ -286,14 +303,38 @@ int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t 
     return KATS_OK;
 }
 
+int launch_filter(const Plan &p, const float *sino, float *gF, void *ws, size_t ws_bytes, cudaStream_t st,
+                  int64_t nv_chunk)
+{
+    kats::NvtxRange nvtx_range("filter (steps 1-6)");
+    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
+    if (ws_bytes < filter_workspace_bytes(p)) {
+        set_error("filter workspace too small: %zu < %zu", ws_bytes, filter_workspace_bytes(p));
+        return KATS_ESPACE;
+    }
+    const int64_t chunk = filter_chunk_views(p, chunk_bytes_per_view(p));
+    float *g3 = (float *)ws;
+    float *g4 = g3 + chunk * p.n_psi * kpad(p);
+    const size_t view_in = (size_t)(p.g.n_rows * p.g.n_cols), view_out = (size_t)(p.g.n_rows * p.gf_cols);
+    for (int64_t v0 = 0; v0 < nv; v0 += chunk) {
+        int rc = filter_pass(p, sino + v0 * view_in, gF + v0 * view_out, g3, g4, std::min(chunk, nv - v0), st);
+        if (rc) return rc;
+    }
+    return KATS_OK;
+}
+
 // ------------------------------------------------------------ transposes
+// Chunk by chunk like the forward filter: per view, region 1 holds g4^T [psi][tct_k] and later g1^T
+// [row][nc1]; region 2 g3^T [psi][tct_n] (rows padded to the tensor-core transpose's K and N); plus
+// one view of g1^T carried from the previous chunk for the derivative's transpose, which couples
+// each sinogram view to the half-grid views on both sides of it.
+static int64_t adj_region1(const Plan &p) { return std::max<int64_t>(p.n_psi * p.tct_k, p.g.n_rows * p.nc1); }
+static size_t adj_bytes_per_view(const Plan &p) { return sizeof(float) * (size_t)(adj_region1(p) + p.n_psi * p.tct_n); }
+
 size_t filter_adjoint_workspace_bytes(const Plan &p)
 {
-    const int64_t nv = p.n_fviews;
-    // region 1: g4^T [v][psi][tct_k], later reused for g1^T [v][row][nc1]; region 2: g3^T [v][psi][tct_n]
-    // (rows padded to the tensor-core transpose's K and N)
-    const int64_t r1 = std::max<int64_t>(p.n_psi * p.tct_k, p.g.n_rows * p.nc1);
-    return sizeof(float) * (size_t)(nv * r1 + nv * p.n_psi * p.tct_n);
+    return adj_bytes_per_view(p) * (size_t)filter_chunk_views(p, adj_bytes_per_view(p)) +
+           sizeof(float) * (size_t)(p.g.n_rows * p.nc1);
 }
 
 // 6^T then 5^T: g4a[v][l][c] = sum_r cos(alpha_c) gF[v][r][c] * (tap weight of l)
@@ -357,56 +398,54 @@ __global__ void k_rebin_T(const float *__restrict__ g3a, float *__restrict__ g1a
 }
 
 // 1^T: each sample gathers the (up to) four half-grid cells that read it.
-__global__ void k_deriv_T(const float *__restrict__ g1a, float *__restrict__ sino, int64_t first_view, int64_t nv,
-                          int64_t n_views, int n_rows, int n_cols, float a_lam, float a_alp)
+// 2^T then 1^T for sinogram views first_view + [k_begin, k_end) (relative view k takes the half-grid
+// views k - 1 and k, each from the chunk's g1^T [c0, c1) or, for view c0 - 1, from the carried one).
+__global__ void k_deriv_T(const float *__restrict__ g1a, const float *__restrict__ carry, float *__restrict__ sino,
+                          int64_t first_view, int64_t nv, int64_t c0, int64_t c1, int64_t k_begin, int64_t k_end,
+                          int n_rows, int n_cols, float a_lam, float a_alp)
 {
     const int nc1 = n_cols - 1;
-    const int64_t per = (int64_t)n_rows * n_cols, total = n_views * per;
+    const int64_t per = (int64_t)n_rows * n_cols, total = (k_end - k_begin) * per;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = t / per;
+        const int64_t k = k_begin + t / per;
         const int rc = (int)(t % per), r = rc / n_cols, c = rc % n_cols;
         float acc = 0.0f;
 #pragma unroll
         for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
             for (int dc = 0; dc < 2; ++dc) {
-                const int64_t kp = k - dk - first_view;
+                const int64_t kp = k - dk;
                 const int cp = c - dc;
                 if (kp < 0 || kp >= nv || cp < 0 || cp >= nc1) continue;
+                const float *src = kp >= c0 ? g1a + (kp - c0) * n_rows * nc1 : carry;
                 const float coef = (dk ? a_lam : -a_lam) + (dc ? a_alp : -a_alp);
-                acc = fmaf(coef, g1a[(kp * n_rows + r) * nc1 + cp], acc);
+                acc = fmaf(coef, src[r * nc1 + cp], acc);
             }
-        sino[t] = acc;
+        sino[(first_view + k) * per + rc] = acc;
     }
 }
 
-int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes, cudaStream_t st)
+// Steps 6^T .. 4^T of views [c0, c1) of gF into the chunk buffers, ending with g1^T in region 1.
+static int filter_adjoint_pass(const Plan &p, const float *gF, float *g4a, float *g3a, int64_t nvc, cudaStream_t st)
 {
-    const int64_t nv = p.n_fviews, nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
+    const int64_t nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi;
     const int64_t Kp4 = p.tct_k, Kp = p.tct_n;  // row strides of g4^T and g3^T
-    if (ws_bytes < filter_adjoint_workspace_bytes(p)) {
-        set_error("filter adjoint workspace too small");
-        return KATS_ESPACE;
-    }
-    const int64_t r1 = std::max<int64_t>(np * Kp4, nr * p.nc1);
-    float *g4a = (float *)ws;
-    float *g3a = g4a + nv * r1;
     float *g1a = g4a;  // g4^T is dead once g3^T is formed
     size_t sm1 = sizeof(float) * 32 * (size_t)np, sm2 = sizeof(float) * 32 * (size_t)nr;
     if (sm1 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_unrebin_cos_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     if (sm2 > 48 * 1024) KATS_CUDA(cudaFuncSetAttribute(k_rebin_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    k_unrebin_cos_T<<<dim3((unsigned)ceil_div(Kp4, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm1, st>>>(
-        gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp4, (int)p.gf_cols);
+    k_unrebin_cos_T<<<dim3((unsigned)ceil_div(Kp4, 32), (unsigned)std::min<int64_t>(nvc, 65535)), 256, sm1, st>>>(
+        gF, g4a, p.psi_idx, p.psi_frac, p.cosa, (int)nvc, (int)nr, (int)nc, (int)np, (int)Kp4, (int)p.gf_cols);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
-    const int64_t M = nv * np;
+    const int64_t M = nvc * np;
     // 4^T: the transposed Toeplitz contraction, on the tensor cores when they can run it
     bool tc = false;
     int rc = launch_hilbert_tc_op(p, g4a, M, p.tct_k, p.btT_hi, p.btT_lo, p.tct_n, g3a, (int)p.tct_n, st, &tc);
     if (rc) return rc;
     if (!tc) {
         if (ceil_div(M, GBM) > 65535) {
-            set_error("too many filtered views for one launch (%lld)", (long long)nv);
+            set_error("too many filtered views for one launch (%lld)", (long long)nvc);
             return KATS_EINVAL;
         }
         k_toeplitz_gemm<<<dim3((unsigned)ceil_div(p.nc1, GBN), (unsigned)ceil_div(M, GBM)), 256, 0, st>>>(
@@ -414,16 +453,47 @@ int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws,
         count_launches(1);
         KATS_CUDA(cudaGetLastError());
     }
-    k_rebin_T<<<dim3((unsigned)ceil_div(p.nc1, 32), (unsigned)std::min<int64_t>(nv, 65535)), 256, sm2, st>>>(
-        g3a, g1a, p.kap_idx, p.kap_frac, p.lw, (int)nv, (int)nr, (int)nc, (int)np, (int)Kp);
+    k_rebin_T<<<dim3((unsigned)ceil_div(p.nc1, 32), (unsigned)std::min<int64_t>(nvc, 65535)), 256, sm2, st>>>(
+        g3a, g1a, p.kap_idx, p.kap_frac, p.lw, (int)nvc, (int)nr, (int)nc, (int)np, (int)Kp);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
+    return KATS_OK;
+}
+
+int launch_filter_adjoint(const Plan &p, const float *gF, float *sino, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const int64_t nv = p.n_fviews, nc = p.g.n_cols, nr = p.g.n_rows;
+    if (ws_bytes < filter_adjoint_workspace_bytes(p)) {
+        set_error("filter adjoint workspace too small");
+        return KATS_ESPACE;
+    }
+    const int64_t chunk = filter_chunk_views(p, adj_bytes_per_view(p));
+    float *g4a = (float *)ws;
+    float *g3a = g4a + chunk * adj_region1(p);
+    float *carry = g3a + chunk * p.n_psi * p.tct_n;  // g1^T of the previous chunk's last view
+    const size_t per = (size_t)(nr * nc), cell = (size_t)(nr * p.nc1);
+    // sinogram views outside the window [first_view, first_view + nv] receive nothing
+    if (p.first_view > 0) KATS_CUDA(cudaMemsetAsync(sino, 0, sizeof(float) * per * (size_t)p.first_view, st));
+    const int64_t tail = p.g.n_views - (p.first_view + nv + 1);
+    if (tail > 0)
+        KATS_CUDA(cudaMemsetAsync(sino + (size_t)(p.first_view + nv + 1) * per, 0, sizeof(float) * per * (size_t)tail,
+                                  st));
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
-    const int64_t total = p.g.n_views * nr * nc;
-    k_deriv_T<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 148 * 64), 256, 0, st>>>(
-        g1a, sino, p.first_view, nv, p.g.n_views, (int)nr, (int)nc, a_lam, a_alp);
-    count_launches(1);
-    KATS_CUDA(cudaGetLastError());
+    for (int64_t c0 = 0; c0 < nv; c0 += chunk) {
+        const int64_t c1 = std::min(c0 + chunk, nv);
+        int rc = filter_adjoint_pass(p, gF + (size_t)c0 * (size_t)(nr * p.gf_cols), g4a, g3a, c1 - c0, st);
+        if (rc) return rc;
+        // sinogram views c0 .. c1 - 1 (and c1 = nv after the last chunk) have every half-grid view they take
+        const int64_t k_end = c1 == nv ? nv + 1 : c1;
+        const int64_t total = (k_end - c0) * (int64_t)per;
+        k_deriv_T<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), (int64_t)p.sm_count * 64), 256, 0, st>>>(
+            g4a, carry, sino, p.first_view, nv, c0, c1, c0, k_end, (int)nr, (int)nc, a_lam, a_alp);
+        count_launches(1);
+        KATS_CUDA(cudaGetLastError());
+        if (c1 < nv)
+            KATS_CUDA(cudaMemcpyAsync(carry, g4a + (size_t)(c1 - 1 - c0) * cell, sizeof(float) * cell,
+                                      cudaMemcpyDeviceToDevice, st));
+    }
     return KATS_OK;
 }
 

@@ -22,10 +22,17 @@ __device__ __forceinline__ uint16_t to16(float v)
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// chunk by chunk like the FP32 filter: g3 16-bit [chunk][n_psi][tc_k16], then g4 fp32 [chunk][n_psi][tc_n]
+static size_t chunk16_bytes_per_view(const Plan &p) { return (size_t)p.n_psi * ((size_t)p.tc_k16 * 2 + (size_t)p.tc_n * 4); }
+static int64_t chunk16_views(const Plan &p) { return filter_chunk_views(p, chunk16_bytes_per_view(p)); }
+static size_t g3_chunk16_bytes(const Plan &p)
+{
+    return ((size_t)(chunk16_views(p) * p.n_psi) * (size_t)p.tc_k16 * 2 + 255) / 256 * 256;
+}
+
 size_t filter16_workspace_bytes(const Plan &p)
 {
-    const int64_t M = p.n_fviews * p.n_psi;
-    return (size_t)M * (size_t)p.tc_k16 * 2 + 256 + (size_t)M * (size_t)p.tc_n * 4;  // g3 16-bit, g4 fp32
+    return g3_chunk16_bytes(p) + (size_t)(chunk16_views(p) * p.n_psi) * (size_t)p.tc_n * 4;
 }
 
 // Steps 1-3 as k_deriv_rebin, output g3 * d_alpha in 16 bits, rows of tc_k16 (zero tail).
@@ -125,20 +132,12 @@ __global__ void __launch_bounds__(256) k_unrebin_cos16(const float *__restrict__
     }
 }
 
-int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
-                    cudaStream_t st, int64_t nv_chunk)
+// Steps 1-6 of views [0, nv) of the given pointers in one pass (nv at most one chunk).
+static int filter16_pass(const Plan &p, int prec, const float *sino, uint32_t *gFp, uint16_t *g3, float *g4,
+                         int64_t nv, cudaStream_t st)
 {
-    kats::NvtxRange nvtx_range("filter16 (steps 1-6)");
-    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
     const int64_t nc = p.g.n_cols, nr = p.g.n_rows, np = p.n_psi, M = nv * np;
-    if (ws_bytes < filter16_workspace_bytes(p)) {
-        set_error("filter workspace too small: %zu < %zu", ws_bytes, filter16_workspace_bytes(p));
-        return KATS_ESPACE;
-    }
     const bool fp16 = prec == KATS_PREC_FP16;
-    uint16_t *g3 = (uint16_t *)ws;
-    // workspace laid out for every view; a chunk uses the front of each part
-    float *g4 = (float *)((char *)ws + ((size_t)(p.n_fviews * np) * (size_t)p.tc_k16 * 2 + 255) / 256 * 256);
     const float a_lam = (float)(1.0 / (2.0 * p.dlam)), a_alp = (float)(1.0 / (2.0 * p.g.d_alpha));
     const float scale = (float)p.g.d_alpha;
     constexpr size_t kCacheMax = 64 * 1024;  // table entries in shared memory up to this size
@@ -173,6 +172,26 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
                                          (int)p.gf_cols, (int)p.tc_n, vpw);
     count_launches(1);
     KATS_CUDA(cudaGetLastError());
+    return KATS_OK;
+}
+
+int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, void *ws, size_t ws_bytes,
+                    cudaStream_t st, int64_t nv_chunk)
+{
+    kats::NvtxRange nvtx_range("filter16 (steps 1-6)");
+    const int64_t nv = nv_chunk < 0 ? p.n_fviews : std::min<int64_t>(nv_chunk, p.n_fviews);
+    if (ws_bytes < filter16_workspace_bytes(p)) {
+        set_error("filter workspace too small: %zu < %zu", ws_bytes, filter16_workspace_bytes(p));
+        return KATS_ESPACE;
+    }
+    const int64_t chunk = chunk16_views(p);
+    uint16_t *g3 = (uint16_t *)ws;
+    float *g4 = (float *)((char *)ws + g3_chunk16_bytes(p));
+    const size_t view_in = (size_t)(p.g.n_rows * p.g.n_cols), view_out = (size_t)((p.g.n_rows + 1) * p.gf_cols);
+    for (int64_t v0 = 0; v0 < nv; v0 += chunk) {
+        int rc = filter16_pass(p, prec, sino + v0 * view_in, gFp + v0 * view_out, g3, g4, std::min(chunk, nv - v0), st);
+        if (rc) return rc;
+    }
     return KATS_OK;
 }
 

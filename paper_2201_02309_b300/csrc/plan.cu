@@ -326,6 +326,36 @@ __global__ void k_plan_psi(DevGeom G, int32_t *idx, float *frac)
     }
 }
 
+// Tile-relative projection table (layout and meaning in Plan::geo): one thread per (tile, view of a
+// turn), FP64.  The window start is the lowest column any of the tile's corner columns (clamped to
+// the volume) reaches in that view, minus one, aligned down to 4 floats (16-byte TMA start).
+__global__ void k_plan_geo(DevGeom G, int ntx, int nty, float4 *geo)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ntx * nty * G.vpt) return;
+    const int t = (int)(i / G.vpt), k = (int)(i % G.vpt);
+    const int tx = t % ntx, ty = t / ntx;
+    const double ph = G.lambda_first + ((double)k + 0.5) * G.dlam + G.lambda0;
+    const double cs = cos(ph), sn = sin(ph);
+    double cmin = 1e300;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t ix = (q & 1) ? min((int64_t)tx * kTileX + kTileX - 1, G.nx - 1) : (int64_t)tx * kTileX;
+        const int64_t iy = (q & 2) ? min((int64_t)ty * kTileY + kTileY - 1, G.ny - 1) : (int64_t)ty * kTileY;
+        const double x = G.x0 + (double)ix * G.dx, y = G.y0 + (double)iy * G.dy;
+        cmin = fmin(cmin, (atan2(-x * sn + y * cs, G.R - x * cs - y * sn) - G.alpha0) / G.d_alpha);
+    }
+    const int clo = ((int)floor(cmin) - 1) & ~3;
+    const double xc = G.x0 + ((double)tx * kTileX + 0.5 * (kTileX - 1)) * G.dx;
+    const double yc = G.y0 + ((double)ty * kTileY + 0.5 * (kTileY - 1)) * G.dy;
+    const double uc = -xc * sn + yc * cs, vc = G.R - xc * cs - yc * sn;
+    const float ur = (float)uc, vr = (float)vc;
+    const double cref = (atan2((double)ur, (double)vr) - G.alpha0) / G.d_alpha - (double)clo;
+    const float chi = (float)cref;
+    geo[2 * i] = make_float4(ur, vr, (float)(uc - (double)ur), (float)(vc - (double)vr));
+    geo[2 * i + 1] = make_float4((float)((double)ur * ur + (double)vr * vr), chi, (float)(cref - (double)chi),
+                                 __int_as_float(clo));
+}
+
 // One-pitch PI table: first/last filtered view and their covered fractions
 // (midpoint rule over [lam_i, lam_o]; hard mode: indicator at l_{k+1/2}).
 __global__ void k_plan_pi(DevGeom G, int32_t *k0, int32_t *k1, float *w0, float *w1, double *lam_i,
@@ -535,7 +565,7 @@ static void free_plan(Plan *p)
     void *ptrs[] = {p->kap_idx, p->kap_frac, p->psi_idx, p->psi_frac, p->pi_k0, p->pi_k1, p->pi_w0,
                     p->pi_w1, p->slice_kmin, p->slice_kmax, p->hk, p->lw, p->cosa, p->trig, p->dev_status,
                     p->bt_hi, p->bt_lo, p->btT_hi, p->btT_lo, p->trig_lo, p->bt16_hi[0], p->bt16_lo[0], p->bt16_hi[1],
-                    p->bt16_lo[1]};
+                    p->bt16_lo[1], p->geo};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -570,7 +600,8 @@ static int build(Plan *p)
         (rc = dalloc(p, &p->bt_hi, p->tc_n * p->tc_k)) || (rc = dalloc(p, &p->bt_lo, p->tc_n * p->tc_k)) ||
         (rc = dalloc(p, &p->btT_hi, p->tct_n * p->tct_k)) || (rc = dalloc(p, &p->btT_lo, p->tct_n * p->tct_k)) ||
         (rc = dalloc(p, &p->bt16_hi[0], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[0], p->tc_n * p->tc_k16)) ||
-        (rc = dalloc(p, &p->bt16_hi[1], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[1], p->tc_n * p->tc_k16)))
+        (rc = dalloc(p, &p->bt16_hi[1], p->tc_n * p->tc_k16)) || (rc = dalloc(p, &p->bt16_lo[1], p->tc_n * p->tc_k16)) ||
+        (rc = dalloc(p, &p->geo, 2 * (size_t)p->geo_ntx * p->geo_nty * g.views_per_turn)))
         return rc;
     // Everything below runs on a private non-blocking stream (host tables are
     // copied with stream-ordered copies, scratch is stream-ordered), so
@@ -671,6 +702,9 @@ static int build(Plan *p)
             if (q) cudaFreeAsync(q, st);
     };
     k_plan_kappa<<<(unsigned)ceil_div(p->n_psi * p->nc1, 256), 256, 0, st>>>(G, p->kap_idx, p->kap_frac);
+    count_launches(1);
+    k_plan_geo<<<(unsigned)ceil_div((int64_t)p->geo_ntx * p->geo_nty * g.views_per_turn, 128), 128, 0, st>>>(
+        G, p->geo_ntx, p->geo_nty, p->geo);
     count_launches(1);
     k_plan_psi<<<(unsigned)ceil_div(nr * nc, 128), 128, 0, st>>>(G, p->psi_idx, p->psi_frac);
     count_launches(1);
@@ -797,6 +831,7 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     Plan *p = new Plan();
     p->g = *g;
     cudaError_t de = cudaGetDevice(&p->device);
+    if (de == cudaSuccess) de = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     if (de != cudaSuccess) {
         delete p;
         return cuda_fail(de, "cudaGetDevice");
@@ -807,6 +842,11 @@ int katsevich_plan(const kats_geometry *g, kats_plan **out)
     p->r_fov = r_fov(*g);
     p->alpha_m = asin(p->r_fov / g->R);
     p->psi_max = 0.5 * kPi + p->alpha_m;
+    p->geo_ntx = (int)ceil_div(g->nx, kTileX);
+    p->geo_nty = (int)ceil_div(g->ny, kTileY);
+    // a voxel's offset from its tile centre over the nearest source distance bounds the tangent of
+    // its angle from the centre's ray
+    p->geo_tmax = (float)(std::hypot(0.5 * (kTileX - 1) * g->dx, 0.5 * (kTileY - 1) * g->dy) / (g->R - p->r_fov));
     p->dpsi = 2.0 * p->psi_max / (double)(p->n_psi - 1);
     p->h = g->P / (2.0 * kPi);
     p->dlam = 2.0 * kPi / (double)g->views_per_turn;

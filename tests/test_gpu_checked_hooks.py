@@ -48,7 +48,10 @@ rep["status_clean"] = native.katsevich_device_status(kp.handle)
 # the timeout path
 native.katsevich_debug_wait_limit(1 << 12)
 native.katsevich_debug_stall_producer(3)
-stalled = kp.recon(d).cpu().numpy()
+stalled = torch.full(kp.vol_shape, float("nan"), device="cuda")  # CTAs that give up store nothing
+kp.recon(d, out=stalled)
+stalled = stalled.cpu().numpy()
+rep["stalled_nan"] = int(np.isnan(stalled).sum())
 rep["status_stalled"] = native.katsevich_device_status(kp.handle)
 rep["status_after_read"] = native.katsevich_device_status(kp.handle)
 rep["stalled_equal_clean"] = bool(np.array_equal(stalled, clean))
@@ -95,7 +98,7 @@ def test_timeout_path_and_general_window_path(tmp_path):
     assert rep["status_clean"] == 0
     assert rep["status_stalled"] == 1  # a bounded device wait gave up
     assert rep["status_after_read"] == 0  # reading the status clears it
-    assert not rep["stalled_equal_clean"]  # the stalled volume is incomplete
+    assert not rep["stalled_equal_clean"] and rep["stalled_nan"] > 0  # the stalled volume is incomplete
     assert rep["served"] == kats.native.KATS_ETIMEOUT
     assert rep["served_after"] and rep["again_equal_clean"] and rep["status_again"] == 0
     assert rep["general_equal_ramp"]

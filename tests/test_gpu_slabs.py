@@ -1,13 +1,15 @@
 """z-slab partition of one volume, the multi-GPU split of a single reconstruction
 (one slab per rank, no exchange between them): a slab computed from only the
 sinogram views it reads equals those slices of the whole-volume reconstruction
-bit for bit, and the views it reads are the union of its voxels' PI windows,
-taken here from the plan's one-pitch k0 / k1 tables shifted by whole turns."""
+(bit for bit where the slab and the whole volume group their slices alike, to FP32
+rounding where the paired-pitch kernel pairs a slice differently), and the views it
+reads are the union of its voxels' PI windows, taken here from the plan's one-pitch
+k0 / k1 tables shifted by whole turns."""
 import numpy as np
 import pytest
 
 import synth
-from cases import multipitch_case
+from cases import close_paths, multipitch_case
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +61,10 @@ def test_multipitch_slabs_equal_whole_volume(kats):
     full = kp.recon(dsino).cpu().numpy()
     for world in (1, 2, 3, 4):
         out, spans = run_slabs(kats, kp, dsino, world, kats.KATS_PREC_FP32)
-        assert np.array_equal(out, full), world
+        if world == 1:  # one slab is the whole volume: the same launch
+            assert np.array_equal(out, full)
+        else:
+            close_paths(out, full, f"{world} slabs")
         # a rank reads far fewer views than the scan holds; neighbours share a halo of views
         if world > 1:
             assert all(b0 < a1 for (_, a1), (b0, _) in zip(spans, spans[1:]))
@@ -99,4 +104,6 @@ def test_slab_errors(kats):
     # a wider window than needed is fine
     w0 = max(vb - 3, 0)
     a = kp.recon_slab(dsino[w0:vb + vc + 5].clone(), w0, 16, 48).cpu().numpy()
-    assert np.array_equal(a, kp.recon(dsino).cpu().numpy()[16:48])
+    b = kp.recon_slab(dsino[vb:vb + vc].clone(), vb, 16, 48).cpu().numpy()
+    assert np.array_equal(a, b)
+    close_paths(a, kp.recon(dsino).cpu().numpy()[16:48], "slab 16:48")
