@@ -734,11 +734,13 @@ __device__ __forceinline__ void view_geo1(const BPArgs &a, float ox, float oy, f
     g.dur = M * a.dz_over_dw;
 }
 
-// Work items of a paired launch: A slices [s0, s0 + T) and B slices [s0 + N, s0 + N + T).
+// Work items of a paired launch: A slices [s0, s0 + cnt) and B slices [s0 + N, s0 + N + cnt), cnt <= T
+// (cnt < T only in a PARTIAL launch).
 constexpr int kMaxPairItems = 64;
 struct PairItems {
     int n;
     int s0[kMaxPairItems];
+    int cnt[kMaxPairItems];
 };
 
 // Paired-pitch backprojection.  A CTA owns B2_TX x B2_TY columns and two groups of T slices one pitch
@@ -752,11 +754,15 @@ struct PairItems {
 // size of PITCH x kPairRows floats, so the B window's offset is a compile-time constant.
 constexpr int kPairRows = 72;
 
-template <int PITCH, int MODE, bool ROWS_OK, int T, int RP>
+// PARTIAL: items with fewer than T slices per group; the missing slices take every view with clamped
+// rows and are not stored (as in k_backproject_tma's PARTIAL form); launched with ROWS_OK false.
+template <int PITCH, int MODE, bool ROWS_OK, int T, int RP, bool PARTIAL = false>
 __global__ void __launch_bounds__(B2_THREADS, 2)
     k_backproject_pair(const __grid_constant__ CUtensorMap gmap, BP2Args p, const __grid_constant__ PairItems it)
 {
+    static_assert(!PARTIAL || !ROWS_OK, "missing slices read clamped rows");
     constexpr int SLOT = PITCH * kPairRows;
+    static_assert(SLOT % 32 == 0, "slots start on 128-byte boundaries (TMA destinations)");
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
     __shared__ float4 s_geo[RP][2];  // the view's table rows (tile reference ray, window start)
@@ -768,7 +774,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const bool producer = warp == B2_CW;
     const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
     const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
-    const int s0 = it.s0[blockIdx.z];
+    const int s0 = it.s0[blockIdx.z], cnt = PARTIAL ? it.cnt[blockIdx.z] : T;
     const bool active = !producer && ix < a.nx && iy < a.ny;
     const int base = (int)(((128u - (smem_addr(smem) & 127u)) & 127u) >> 2);
 
@@ -785,7 +791,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             ka[t] = INT32_MAX;
             kb[t] = INT32_MIN;
             wa[t] = wb[t] = 0.0f;
-            if (active) {
+            if (active && t < cnt) {
                 const int j = s % a.N, m = s / a.N;
                 const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
                 ka[t] = a.k0[o] + m * a.vpt;
@@ -795,8 +801,10 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 kmin = min(kmin, ka[t]);
                 kmax = max(kmax, kb[t]);
             }
-            kfull_lo = max(kfull_lo, ka[t]);
-            kfull_hi = min(kfull_hi, kb[t]);
+            if (!(PARTIAL && active && t >= cnt)) {
+                kfull_lo = max(kfull_lo, ka[t]);
+                kfull_hi = min(kfull_hi, kb[t]);
+            }
         }
         if (!p.mono) {
             kfull_lo = INT32_MAX;
@@ -807,8 +815,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         for (int t = 0; t < T / 2; ++t) accA[t] = accB[t] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            lo[t] = (float)(ka[t] - kbase) - wa[t];
-            hi[t] = (float)(kb[t] - kbase) + wb[t];
+            const bool missing = PARTIAL && t >= cnt;  // open in every view, not stored
+            lo[t] = missing ? -3.0e9f : (float)(ka[t] - kbase) - wa[t];
+            hi[t] = missing ? 3.0e9f : (float)(kb[t] - kbase) + wb[t];
         }
     }
     if (tid == 0) {
@@ -928,6 +937,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     if (!active) return;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
+        if (PARTIAL && t >= cnt) break;
         const float va = (t & 1) ? accA[t >> 1].y : accA[t >> 1].x;
         const float vb = (t & 1) ? accB[t >> 1].y : accB[t >> 1].x;
         a.vol[((int64_t)(s0 + t) * a.ny + iy) * a.nx + ix] = va * p.out_scale;
@@ -1029,45 +1039,38 @@ static int window_cols(const Plan &p)
 }
 
 // Decomposition of slices [S0, S1) for the paired kernel: from S0 on, blocks of 2N slices whose
-// first N pair with the next N; each block's pairs [a, a + L) go in items of T slices (T of the
-// instantiated 12, 14 leaving the fewest slices unpaired, the larger on a tie), the rest are
-// ranges for the single kernel.  False when the launch holds no full item.
+// first L <= N slices pair with the slices N further on.  A block's L pairs go in items of T slices,
+// T of the instantiated 14 and 12 whichever leaves fewer idle slots (the larger on a tie), the last
+// item partial when T does not divide L; the slices without a partner are ranges for the single
+// kernel.  False when the launch holds no pair.
+struct PairItem {
+    int T, s0, cnt;
+};
 struct PairPlan {
-    int T = 0;
-    std::vector<int> items;                  // first A slice of each item
+    std::vector<PairItem> items;
     std::vector<std::pair<int, int>> rest;  // unpaired slice ranges [s, e)
 };
 
 static bool pair_plan(int S0, int S1, int N, PairPlan *out)
 {
-    PairPlan best;
-    int best_rest = INT32_MAX;
-    for (int T : {14, 12}) {
-        PairPlan pp;
-        pp.T = T;
-        int a0 = S0, n_rest = 0;
-        auto add_rest = [&](int s, int e) {
-            if (e <= s) return;
-            if (!pp.rest.empty() && pp.rest.back().second == s)
-                pp.rest.back().second = e;
-            else
-                pp.rest.push_back({s, e});
-            n_rest += e - s;
-        };
-        for (; a0 + N < S1; a0 += 2 * N) {
-            const int L = std::min(N, S1 - a0 - N), nfull = L / T;
-            for (int i = 0; i < nfull; ++i) pp.items.push_back(a0 + i * T);
-            add_rest(a0 + nfull * T, a0 + N);
-            add_rest(a0 + N + nfull * T, std::min(a0 + 2 * N, S1));
-        }
-        add_rest(a0, S1);
-        if (!pp.items.empty() && n_rest < best_rest) {
-            best_rest = n_rest;
-            best = pp;
-        }
+    PairPlan pp;
+    auto add_rest = [&](int s, int e) {
+        if (e <= s) return;
+        if (!pp.rest.empty() && pp.rest.back().second == s)
+            pp.rest.back().second = e;
+        else
+            pp.rest.push_back({s, e});
+    };
+    int a0 = S0;
+    for (; a0 + N < S1; a0 += 2 * N) {
+        const int L = std::min(N, S1 - a0 - N);
+        const int T = 12 * (int)ceil_div(L, 12) < 14 * (int)ceil_div(L, 14) ? 12 : 14;
+        for (int i = 0; i < L; i += T) pp.items.push_back({T, a0 + i, std::min(T, L - i)});
+        add_rest(a0 + L, a0 + N);
     }
-    if (best.items.empty()) return false;
-    *out = best;
+    add_rest(a0, S1);
+    if (pp.items.empty()) return false;
+    *out = pp;
     return true;
 }
 
@@ -1117,10 +1120,13 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned gx = (unsigned)ceil_div(p.g.nx, B2_TX), gy = (unsigned)ceil_div(p.g.ny, B2_TY);
     // slices [s, e) in 16-slice z tiles
-    // slices [s, e) in 16-slice z tiles; without view ranges a last partial tile goes to the PARTIAL form
+    // slices [s, e) in 16-slice z tiles; without view ranges a last partial tile of at least half a
+    // tile goes to the PARTIAL form (a smaller one costs less on the weighted path, which skips the
+    // missing slices' pairs)
     auto single = [&](int s, int e) -> int {
         if (e <= s) return KATS_OK;
-        const int e_full = ranged ? e : s + (e - s) / B2_T * B2_T;
+        const int rem = (e - s) % B2_T;
+        const int e_full = ranged || rem < B2_T / 2 ? e : e - rem;
         BP2Args bs = b;
         if (e_full > s) {
             bs.a.s_begin = s;
@@ -1148,17 +1154,32 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     const size_t pair_smem = sizeof(float) * (size_t)PITCH * kPairRows * 2 * 3 + 128;  // 3 slot pairs
     if (!ranged && PITCH <= 64 && srows <= kPairRows && pair_smem <= kTwoPerSm &&
         pair_plan(a.s_begin, a.s_end, (int)p.N, &pp)) {
-        auto pk = pp.T == 12 ? (rows_ok ? k_backproject_pair<PITCH, MODE, true, 12, 3> : k_backproject_pair<PITCH, MODE, false, 12, 3>)
-                             : (rows_ok ? k_backproject_pair<PITCH, MODE, true, 14, 3> : k_backproject_pair<PITCH, MODE, false, 14, 3>);
-        KATS_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
-        for (size_t i0 = 0; i0 < pp.items.size(); i0 += kMaxPairItems) {
-            PairItems it;
-            it.n = (int)std::min<size_t>(kMaxPairItems, pp.items.size() - i0);
-            for (int i = 0; i < it.n; ++i) it.s0[i] = pp.items[i0 + (size_t)i];
-            pk<<<dim3(gx, gy, (unsigned)it.n), B2_THREADS, pair_smem, st>>>(map, b, it);
-            count_launches(1);
-            KATS_CUDA(cudaGetLastError());
-        }
+        // one launch per (T, full or partial) group of items
+        for (int T : {14, 12})
+            for (int partial = 0; partial < 2; ++partial) {
+                std::vector<PairItem> grp;
+                for (const PairItem &i : pp.items)
+                    if (i.T == T && (i.cnt < T) == (partial != 0)) grp.push_back(i);
+                if (grp.empty()) continue;
+                auto pk = partial ? (T == 12 ? k_backproject_pair<PITCH, MODE, false, 12, 3, true>
+                                             : k_backproject_pair<PITCH, MODE, false, 14, 3, true>)
+                                  : (T == 12 ? (rows_ok ? k_backproject_pair<PITCH, MODE, true, 12, 3>
+                                                        : k_backproject_pair<PITCH, MODE, false, 12, 3>)
+                                             : (rows_ok ? k_backproject_pair<PITCH, MODE, true, 14, 3>
+                                                        : k_backproject_pair<PITCH, MODE, false, 14, 3>));
+                KATS_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
+                for (size_t i0 = 0; i0 < grp.size(); i0 += kMaxPairItems) {
+                    PairItems it;
+                    it.n = (int)std::min<size_t>(kMaxPairItems, grp.size() - i0);
+                    for (int i = 0; i < it.n; ++i) {
+                        it.s0[i] = grp[i0 + (size_t)i].s0;
+                        it.cnt[i] = grp[i0 + (size_t)i].cnt;
+                    }
+                    pk<<<dim3(gx, gy, (unsigned)it.n), B2_THREADS, pair_smem, st>>>(map, b, it);
+                    count_launches(1);
+                    KATS_CUDA(cudaGetLastError());
+                }
+            }
         for (const auto &r : pp.rest) {
             int rc = single(r.first, r.second);
             if (rc) return rc;
