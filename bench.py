@@ -365,8 +365,9 @@ def run_ours(args):
         tex32 = kats.native.katsevich_tex_bilinear_rate(False)
         tex16 = kats.native.katsevich_tex_bilinear_rate(True)
         updates_per_s = info["update_count"] / (t_bp / 1e3)
-        roofline = {"kernel": "k_backproject_tma", "bound": "alu", "achieved": achieved, "peak": smem_peak,
-                    "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("k_backproject_tma"),
+        roofline = {"kernel": "backprojection (k_backproject_pair + k_backproject_tma, one reconstruction's launches)",
+                    "bound": "alu", "achieved": achieved, "peak": smem_peak,
+                    "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("backprojection"),
                     "peak_source": f"shared-memory data path: 148 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk_kind} clock)",
                     "peak_measured": smem_measured, "frac_of_measured": achieved / smem_measured,
                     "tex_bilinear_gsamples_per_s": {"fp32": tex32 / 1e9, "fp16": tex16 / 1e9},

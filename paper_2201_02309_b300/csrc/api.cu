@@ -132,12 +132,22 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     // slabs of whole 16-slice z tiles.  The first four are small: the first starts backprojecting
     // after a few chunks, and each further 16 slices need only about a chunk more of views, which
     // arrive faster than a small slab is backprojected, so the GPU is not left waiting for the
-    // copies; the middle slabs are up to 128 slices (fewer partly filled last waves), the last small
-    // again (little to copy back at the end)
+    // copies.  Then, where the volume holds them, 2N slices in one slab, whose halves the paired
+    // kernel reconstructs together (its views have arrived by the time the small slabs are done);
+    // the rest in slabs of up to 128 slices, the last 16 (little to copy back at the end).
+    // Measured on the clinical workload: 16 x 4, 140, 36, 16 in 43.1 ms against 44.1 ms for 16 x 4,
+    // 128, 48, 16.
     std::vector<int> slab_lo{0};
+    const int64_t pair_slab = 2 * p.N;
     while (slab_lo.back() < nz) {
         const int64_t s0 = slab_lo.back(), left = nz - s0;
-        const int64_t n = s0 < 64 ? 16 : (left <= 144 ? (left > 16 ? (left - 16 + 15) / 16 * 16 : left) : 128);
+        int64_t n;
+        if (s0 < 64)
+            n = 16;
+        else if (left >= pair_slab + 16 && s0 < 64 + pair_slab)
+            n = pair_slab;
+        else
+            n = left <= 144 ? (left > 32 ? left - 16 : left) : 128;
         slab_lo.push_back((int)std::min<int64_t>(nz, s0 + std::max<int64_t>(n, 1)));
     }
     const int n_slabs = (int)slab_lo.size() - 1;
