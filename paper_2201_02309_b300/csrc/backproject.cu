@@ -479,6 +479,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 {
     static_assert(!PARTIAL || !ROWS_OK, "a partial tile's missing slices read clamped rows");
     extern __shared__ __align__(128) float smem[];
+    // a backprojection launch that follows this one on the stream (other slices, same inputs) may
+    // start its CTAs while this grid's last wave drains
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
     __shared__ float4 s_geo[RP][4];  // the pair's two views' table rows (tile reference rays, window start)
     __shared__ float4 s_cs[RP];      // (cos, sin) of the pair's two views
@@ -764,6 +767,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     constexpr int SLOT = PITCH * kPairRows;
     static_assert(SLOT % 32 == 0, "slots start on 128-byte boundaries (TMA destinations)");
     extern __shared__ __align__(128) float smem[];
+    // a backprojection launch that follows this one on the stream (other slices, same inputs) may
+    // start its CTAs while this grid's last wave drains
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
     __shared__ float4 s_geo[RP][2];  // the view's table rows (tile reference ray, window start)
     __shared__ float2 s_cs[RP];      // its (cos, sin)
@@ -1120,6 +1126,25 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned gx = (unsigned)ceil_div(p.g.nx, B2_TX), gy = (unsigned)ceil_div(p.g.ny, B2_TY);
     // slices [s, e) in 16-slice z tiles
+    // The launches of one call write disjoint slices from inputs complete before the first starts, so
+    // each launch after the first may begin while the previous one's last wave drains (programmatic
+    // dependent launch; measured 33.5 -> 33.0 ms at config 2).  Launches over a share of the views
+    // continue each other's sums and stay fully ordered.
+    int n_launched = 0;
+    auto launch = [&](auto kernel, dim3 grid, size_t shm, auto... args) -> cudaError_t {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(B2_THREADS);
+        cfg.dynamicSmemBytes = shm;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = (!ranged && n_launched > 0) ? 1 : 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ++n_launched;
+        return cudaLaunchKernelEx(&cfg, kernel, args...);
+    };
     // slices [s, e) in 16-slice z tiles; without view ranges a last partial tile of at least half a
     // tile goes to the PARTIAL form (a smaller one costs less on the weighted path, which skips the
     // missing slices' pairs)
@@ -1131,7 +1156,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
         if (e_full > s) {
             bs.a.s_begin = s;
             bs.a.s_end = e_full;
-            kern<<<dim3(gx, gy, (unsigned)ceil_div(e_full - s, B2_T)), B2_THREADS, smem, st>>>(map, bs);
+            KATS_CUDA(launch(kern, dim3(gx, gy, (unsigned)ceil_div(e_full - s, B2_T)), smem, map, bs));
             count_launches(1);
             KATS_CUDA(cudaGetLastError());
         }
@@ -1141,7 +1166,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
             KATS_CUDA(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             bs.a.s_begin = e_full;
             bs.a.s_end = e;
-            kp<<<dim3(gx, gy, 1), B2_THREADS, smem, st>>>(map, bs);
+            KATS_CUDA(launch(kp, dim3(gx, gy, 1), smem, map, bs));
             count_launches(1);
             KATS_CUDA(cudaGetLastError());
         }
@@ -1175,7 +1200,7 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
                         it.s0[i] = grp[i0 + (size_t)i].s0;
                         it.cnt[i] = grp[i0 + (size_t)i].cnt;
                     }
-                    pk<<<dim3(gx, gy, (unsigned)it.n), B2_THREADS, pair_smem, st>>>(map, b, it);
+                    KATS_CUDA(launch(pk, dim3(gx, gy, (unsigned)it.n), pair_smem, map, b, it));
                     count_launches(1);
                     KATS_CUDA(cudaGetLastError());
                 }
