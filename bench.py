@@ -420,8 +420,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not slabs:
-        cpu = oracle_sample(g, sino_np, info)
+        # the host is shared: the median of three runs of the sample
+        runs = sorted((oracle_sample(g, sino_np, info) for _ in range(3)), key=lambda r: r["value"])
+        cpu = runs[1]
         cpu.pop("seconds", None)
+        cpu["sample"] += "; median of 3 runs (%.3f / %.3f / %.3f GUPS)" % tuple(r["value"] for r in runs)
 
     forms = None
     if rank == 0 and world == 1 and not slabs and not args.no_forms and args.precision == "fp32" and \
