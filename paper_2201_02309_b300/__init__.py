@@ -192,7 +192,9 @@ class Plan:
     def recon_slab(self, sino_views, view_begin: int, s_begin: int, s_end: int, out=None,
                    precision=KATS_PREC_FP32, stream=None, workspace=None):
         """Slices [s_begin, s_end) (s_begin a multiple of 16) from sinogram views
-        [view_begin, view_begin + len(sino_views)); equal bit for bit to those slices of recon()."""
+        [view_begin, view_begin + len(sino_views)); equal to those slices of recon() to FP32
+        rounding (the backprojection groups slices one or more pitches apart within a launch, so a
+        slab can group a slice differently from the whole volume)."""
         torch = _torch()
         g = self.geom
         if sino_views.dtype != torch.float32 or not sino_views.is_cuda or not sino_views.is_contiguous():

@@ -28,7 +28,7 @@ def deps():
 
 LIB_DEBUG = os.path.join(LIBDIR, "libkatsevich_debug.so")
 # sources whose kernels carry KATS_DEBUG_CHECKS invariant checks (the bounds-checked build)
-DEBUG_SOURCES = {"backproject.cu"}
+DEBUG_SOURCES = {"backproject.cu", "backproject_multi.cu"}
 
 
 def up_to_date(lib: str = LIB) -> bool:

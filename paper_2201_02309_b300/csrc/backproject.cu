@@ -30,87 +30,14 @@
 #include <utility>
 #include <vector>
 
-#include "common.cuh"
+#include "bp_staged.cuh"
 
 namespace kats {
 
-// Invariant checks of the staged-window kernels, compiled in with KATS_DEBUG_CHECKS (the
-// bounds-checked build that stands in for a memory checker): bit 1 a backprojection tap column
-// outside the CTA's staged columns, bit 2 an unclamped backprojection tap row outside the staged
-// rows, bit 4 / 8 the same for the adjoint's window.  A violation is recorded and the access is
-// clamped into the window, so the checked build never touches shared memory outside it.
-__device__ int g_debug_flags = 0;
-
-#ifdef KATS_DEBUG_CHECKS
-#define KATS_DCHECK(ok, bit)                                  \
-    do {                                                      \
-        if (!(ok)) atomicOr(&::kats::g_debug_flags, (bit));   \
-    } while (0)
-#else
-#define KATS_DCHECK(ok, bit) \
-    do {                     \
-    } while (0)
-#endif
 
 constexpr int BP_T = 8;  // slices per thread
 constexpr int BP_BX = 16, BP_BY = 8;
 
-struct BPArgs {
-    const float *gF;  // [n_fviews][n_rows][gcols], view 0 = half-view first_view
-    float *vol;       // [nz][ny][nx]
-    const int32_t *k0, *k1;
-    const float *w0, *w1;
-    const float2 *trig, *trig_lo;
-    int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
-    int s_begin, s_end;  // slices [s_begin, s_end) of this launch; s_begin a multiple of the z tile
-    // views [k_lo, k_hi] of this launch (backprojection only).  acc_in: the volume holds the raw
-    // sums of the views below k_lo and the launch continues them; acc_final: scale and store the
-    // result, else store raw sums for a later launch.  A split run adds every view in the order
-    // of one launch, so its result is bit for bit that of one launch.
-    int k_lo, k_hi, acc_in, acc_final;
-    int64_t first_view;
-    float R, D, x0, y0, dx, dy;
-    float alpha0, inv_da, w0row, inv_dw, dz_over_dw, scale;
-    // FP64 terms for z - z_src: z_first + s dz - z0 - h (lambda_first + (k + 1/2) dl)
-    double z_first, dz, z0, h, lambda_first, dlam;
-    float hdl, hdl_lo;  // h dl as float plus its rounding residual
-    float K_hi, K_lo;   // alpha0 / d_alpha as float plus its rounding residual
-};
-
-// Detector column of angle alpha, given p = alpha / d_alpha, as integer ci and
-// fraction fc.  Keeping the large constant alpha0 / d_alpha (hi + lo) out of
-// the rounded fraction bounds the error by about 2 ulp(p) instead of
-// ulp(n_cols / 2): this matters for the transpose, whose splat weights carry
-// the coordinate error times the value itself.
-__device__ __forceinline__ void column_split(const BPArgs &a, float p, int *ci, float *fc)
-{
-    const float cf = floorf((p - a.K_hi) - a.K_lo);
-    *ci = (int)cf;
-    *fc = (p - (cf + a.K_hi)) - a.K_lo;
-}
-
-// Per-view source geometry with the trig table carried as float hi + lo, so
-// u* and v* keep FP32 precision relative to themselves (the table's own
-// rounding would otherwise add ~1e-7 x radius of absolute error).
-__device__ __forceinline__ void view_uv(const BPArgs &a, float2 cs, float2 cl, float x, float y, float *u, float *v)
-{
-    *u = fmaf(-x, cs.y, fmaf(y, cs.x, fmaf(-x, cl.y, y * cl.x)));
-    *v = fmaf(-x, cs.x, fmaf(-y, cs.y, fmaf(-x, cl.x, fmaf(-y, cl.y, a.R))));
-}
-
-// z_s - z_src(kbase + kf) for a thread whose slice offset at kbase is zb + zb_lo.
-__device__ __forceinline__ float z_rel(const BPArgs &a, float zb, float zb_lo, float kf)
-{
-    return fmaf(-a.hdl, kf, zb) + fmaf(-a.hdl_lo, kf, zb_lo);
-}
-
-// zb (float) and its residual for slice s0 and view kbase.
-__device__ __forceinline__ void z_base(const BPArgs &a, int s0, int kbase, float *zb, float *zb_lo)
-{
-    const double z = a.z_first + (double)s0 * a.dz - a.z0 - a.h * (a.lambda_first + ((double)kbase + 0.5) * a.dlam);
-    *zb = (float)z;
-    *zb_lo = (float)(z - (double)*zb);
-}
 
 __device__ __forceinline__ float tap(const float *view, int r, int c, int n_rows, int n_cols, int gcols)
 {
@@ -195,279 +122,6 @@ __global__ void __launch_bounds__(BP_BX *BP_BY) k_backproject(BPArgs a)
     }
 }
 
-// ---------------------------------------------------------------- TMA kernel
-// CTA = B2_TX x B2_TY columns x B2_T slices: B2_CW consumer warps (one thread
-// per column) plus one producer warp that stages each view's detector window
-// into a ring of shared-memory slots.  Consumers take two views per
-// iteration, so the slots go in pairs, each pair with one full / empty
-// mbarrier: one wait and one release per two views.  The ring holds RP
-// pairs, 3 or 2 (chosen at launch from the slot size).
-constexpr int B2_TX = kTileX, B2_TY = kTileY, B2_T = 16;
-constexpr int B2_CW = B2_TX * B2_TY / 32;       // consumer warps
-constexpr int B2_THREADS = (B2_CW + 1) * 32;    // + producer warp
-constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
-
-#ifdef KATS_DEBUG_CHECKS
-// Checked build only, for the test of the timeout path: a lower poll limit, and a producer that
-// stops issuing after this many view pairs (-1: never), so that the consumers' waits run out
-// without any copy in flight.  Set by katsevich_debug_wait_limit / katsevich_debug_stall_producer.
-__device__ int g_debug_wait_limit = kWaitLimit;
-__device__ int g_debug_stall_pairs = -1;
-#define KATS_BP_WAIT_LIMIT ::kats::g_debug_wait_limit
-#else
-#define KATS_BP_WAIT_LIMIT kWaitLimit
-#endif
-
-// The staged kernels measure a voxel's detector column from its tile centre's ray: with the
-// centre's (u_r, v_r) from the plan's table and the voxel's offset (du, dv) from it, the angle
-// between the two rays is atan(cross / dot), cross = du v_r - dv u_r, dot = r2 + du u_r + dv v_r,
-// small (|cross / dot| <= kTileTanMax) and formed without cancellation.  Its arctan is the Taylor
-// series to t^11 (truncation below t^13 / 13 <= 6e-10 at the bound).
-constexpr float kTileTanMax = 0.25f;
-
-struct BP2Args {
-    BPArgs a;
-    int W;            // columns of the staged box any voxel of the tile can touch (<= PITCH)
-    int srows;        // staged rows: n_rows + 3 (row 0 and rows n_rows+1.. are zero fill)
-    int slot_floats;  // floats per staged view, multiple of 32 (128-byte slots)
-    int *status;
-    float out_scale;  // dl / 2pi, divided by d_alpha for the scaled 16-bit storage
-    int mono;         // window starts and ends nondecreasing in the slice (plan check)
-    const float4 *geo;  // the plan's tile-relative projection table [tile][view of a turn][2]
-    int geo_ntx;        // tiles per row of the table
-};
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    for (int i = 0; i < KATS_BP_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-            "r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// arctan(t) for |t| <= kTileTanMax: t (1 - t^2 / 3 + t^4 / 5 - t^6 / 7 + t^8 / 9 - t^10 / 11)
-__device__ __forceinline__ float atan_small(float t)
-{
-    const float s = t * t;
-    float p = fmaf(s, -1.0f / 11.0f, 1.0f / 9.0f);
-    p = fmaf(s, p, -1.0f / 7.0f);
-    p = fmaf(s, p, 1.0f / 5.0f);
-    p = fmaf(s, p, -1.0f / 3.0f);
-    return fmaf(t * s, p, t);
-}
-
-// Two slices' taps: bilinear samples at column colx + fc and rows ur2.x,
-// ur2.y of the staged window, smem[colx + (row << log2 PITCH)] (colx carries
-// the -2^23 row-bias of the floor trick, in modulo-2^32 arithmetic), in packed
-// FP32x2 arithmetic: every component is rounded exactly as the scalar tap rounds it
-// (a - b is formed as fma(b, -1, a)), at half the instruction count.  The
-// 16-bit forms read row-pair words (g[r-1][c] low, g[r][c] high): fp16 lerps
-// the column pair in half2 as the scalar tap does, bf16 unpacks exactly to
-// FP32 first.
-template <int PITCH, int MODE, bool CLAMP>
-__device__ __forceinline__ void bp_tap2(const float *smem, uint32_t colx, float2 fc2, __half2 fch, float2 ur2,
-                                        float rmax, float2 w2, float2 &acc2)
-{
-    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-    if (CLAMP) {
-        ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
-        ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
-    } else {
-#ifdef KATS_DEBUG_CHECKS
-        if (!(ur2.x >= 0.0f && ur2.x <= rmax && ur2.y >= 0.0f && ur2.y <= rmax)) {
-            atomicOr(&g_debug_flags, 2);
-            ur2.x = fminf(fmaxf(ur2.x, 0.0f), rmax);
-            ur2.y = fminf(fmaxf(ur2.y, 0.0f), rmax);
-        }
-#endif
-    }
-    const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 yv = __fadd2_rd(ur2, make_float2(8388608.0f, 8388608.0f));  // 2^23 + floor(ur)
-    const uint32_t q0 = colx + ((uint32_t)__float_as_int(yv.x) << SH);
-    const uint32_t q1 = colx + ((uint32_t)__float_as_int(yv.y) << SH);
-    const float2 fr = __ffma2_rn(__fadd2_rn(yv, make_float2(-8388608.0f, -8388608.0f)), m1, ur2);
-    float2 top, bot;
-    if (MODE == 0) {
-        const float2 v00 = make_float2(smem[q0], smem[q1]);
-        const float2 v01 = make_float2(smem[q0 + 1], smem[q1 + 1]);
-        const float2 v10 = make_float2(smem[q0 + PITCH], smem[q1 + PITCH]);
-        const float2 v11 = make_float2(smem[q0 + PITCH + 1], smem[q1 + PITCH + 1]);
-        top = __ffma2_rn(fc2, __ffma2_rn(v00, m1, v01), v00);
-        bot = __ffma2_rn(fc2, __ffma2_rn(v10, m1, v11), v10);
-    } else if (MODE == 2) {
-        const __half2 *h = reinterpret_cast<const __half2 *>(smem);
-        const __half2 c0 = __hfma2(fch, __hsub2(h[q0 + 1], h[q0]), h[q0]);
-        const __half2 c1 = __hfma2(fch, __hsub2(h[q1 + 1], h[q1]), h[q1]);
-        top = make_float2(__low2float(c0), __low2float(c1));
-        bot = make_float2(__high2float(c0), __high2float(c1));
-    } else {
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(smem);
-        const uint32_t a0 = w[q0], b0 = w[q0 + 1], a1 = w[q1], b1 = w[q1 + 1];
-        const float2 ta = make_float2(__uint_as_float(a0 << 16), __uint_as_float(a1 << 16));
-        const float2 tb = make_float2(__uint_as_float(b0 << 16), __uint_as_float(b1 << 16));
-        const float2 ba = make_float2(__uint_as_float(a0 & 0xFFFF0000u), __uint_as_float(a1 & 0xFFFF0000u));
-        const float2 bb = make_float2(__uint_as_float(b0 & 0xFFFF0000u), __uint_as_float(b1 & 0xFFFF0000u));
-        top = __ffma2_rn(fc2, __ffma2_rn(ta, m1, tb), ta);
-        bot = __ffma2_rn(fc2, __ffma2_rn(ba, m1, bb), ba);
-    }
-    acc2 = __ffma2_rn(w2, __ffma2_rn(fr, __ffma2_rn(top, m1, bot), top), acc2);
-}
-
-// One view's contribution to a thread's B2_T slices, in slice pairs.
-// WEIGHTED: the view ends some slice's PI window (end weights, zero outside
-// it; a pair with neither slice in its window is skipped, one with a single
-// such slice still loads its taps, so weighted pairs always clamp);
-// otherwise every slice takes the view with weight 1.
-// T: the thread's slices (T / 2 pairs).  SOFF > 0: a second set of T slices one pitch up (accumulators
-// accB) reads the same taps, positions and weights from the window SOFF floats further on (a
-// compile-time offset, so its loads reuse the first set's addresses): the slice one pitch up sees the
-// view one turn later exactly as this slice sees this view (Sec. II periodicity).
-template <int PITCH, int MODE, bool WEIGHTED, bool CLAMP, int T = B2_T, int SOFF = 0>
-__device__ __forceinline__ void bp_view(const float *smem, uint32_t colx, float fc, float ur0, float dur, float rmax,
-                                        float inv_v, float kf, const float *lo, const float *hi, float2 *acc2,
-                                        float2 *accB = nullptr)
-{
-    const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
-    const __half2 fch = __float2half2_rn(fc);
-#pragma unroll
-    for (int pr = 0; pr < T / 2; ++pr) {
-        const float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
-        if (WEIGHTED) {
-            const float2 om = __fmul2_rn(make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1])),
-                                         make_float2(__saturatef(hi[2 * pr] - kf), __saturatef(hi[2 * pr + 1] - kf)));
-            if (om.x == 0.0f && om.y == 0.0f) continue;
-            const float2 w2 = __fmul2_rn(om, make_float2(inv_v, inv_v));
-            bp_tap2<PITCH, MODE, true>(smem, colx, fc2, fch, ur2, rmax, w2, acc2[pr]);
-            if (SOFF) bp_tap2<PITCH, MODE, true>(smem + SOFF, colx, fc2, fch, ur2, rmax, w2, accB[pr]);
-        } else {
-            bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), acc2[pr]);
-            if (SOFF) bp_tap2<PITCH, MODE, CLAMP>(smem + SOFF, colx, fc2, fch, ur2, rmax, make_float2(inv_v, inv_v), accB[pr]);
-        }
-    }
-}
-
-// One view in a ramp of the thread's slice windows, the windows nondecreasing in
-// the slice.  IN: no slice has ended and some have not started, so the slices
-// the view reaches are a prefix with weights sat(k - lo); otherwise every slice
-// has started, the open ones are a suffix with weights sat(hi - k).  The pair
-// loop stops at the first pair outside; in a boundary pair the closed slice reads
-// its partner's rows (its weight is 0), so the rows stay inside the staged window
-// without clamping.  The weights and taps equal the general weighted path's.
-template <int PITCH, int MODE, bool IN, bool CLAMP, int T = B2_T, int SOFF = 0>
-__device__ __forceinline__ void bp_view_ramp(const float *smem, uint32_t colx, float fc, float ur0, float dur,
-                                             float rmax, float inv_v, float kf, const float *lo, const float *hi,
-                                             float2 *acc2, float2 *accB = nullptr)
-{
-    const float2 fc2 = make_float2(fc, fc), dur2 = make_float2(dur, dur), ur02 = make_float2(ur0, ur0);
-    const float2 iv2 = make_float2(inv_v, inv_v);
-    const __half2 fch = __float2half2_rn(fc);
-#pragma unroll
-    for (int i = 0; i < T / 2; ++i) {
-        const int pr = IN ? i : T / 2 - 1 - i;
-        if (IN ? !(kf > lo[2 * pr]) : !(kf < hi[2 * pr + 1])) break;
-        float2 ur2 = __ffma2_rn(make_float2(2 * pr, 2 * pr + 1), dur2, ur02);
-        const float2 om = IN ? make_float2(__saturatef(kf - lo[2 * pr]), __saturatef(kf - lo[2 * pr + 1]))
-                             : make_float2(__saturatef(hi[2 * pr] - kf), __saturatef(hi[2 * pr + 1] - kf));
-        if (!CLAMP) {
-            if (IN && om.y == 0.0f) ur2.y = ur2.x;
-            if (!IN && om.x == 0.0f) ur2.x = ur2.y;
-        }
-        const float2 w2 = __fmul2_rn(om, iv2);
-        bp_tap2<PITCH, MODE, CLAMP>(smem, colx, fc2, fch, ur2, rmax, w2, acc2[pr]);
-        if (SOFF) bp_tap2<PITCH, MODE, CLAMP>(smem + SOFF, colx, fc2, fch, ur2, rmax, w2, accB[pr]);
-    }
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Geometry of two consecutive views for one voxel column, in FP32x2, from the tile's reference
-// rays (table rows gA0 gA1 / gB0 gB1 of the two views, cs = (cos, sin) of both): the column index
-// relative to the staged window's first column and its fraction (the floor taken as 1.5 * 2^23 +
-// floor(c) rounded down), first staged row of slice 0, row step per slice, and 1/v*.  (ox, oy): the
-// voxel's offset from its tile centre.
-struct ViewGeo2 {
-    float2 fc, ur0, dur, inv_v;
-    int ci0, ci1;
-};
-
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-
-__device__ __forceinline__ void view_geo2(const BPArgs &a, float ox, float oy, float4 cs, float4 gA0, float4 gA1,
-                                          float4 gB0, float4 gB1, float zb, float zb_lo, float kfA, ViewGeo2 &g)
-{
-    const float2 m1 = f2(-1.0f);
-    const float2 c = make_float2(cs.x, cs.z), sn = make_float2(cs.y, cs.w);
-    const float2 ur = make_float2(gA0.x, gB0.x), vr = make_float2(gA0.y, gB0.y);
-    const float2 du = __ffma2_rn(f2(-ox), sn, __ffma2_rn(f2(oy), c, make_float2(gA0.z, gB0.z)));
-    const float2 dv = __ffma2_rn(f2(-ox), c, __ffma2_rn(f2(-oy), sn, make_float2(gA0.w, gB0.w)));
-    const float2 cross = __ffma2_rn(du, vr, __fmul2_rn(dv, __fmul2_rn(ur, m1)));
-    const float2 dot = __ffma2_rn(ur, du, __ffma2_rn(vr, dv, make_float2(gA1.x, gB1.x)));
-    const float2 t = __fmul2_rn(cross, make_float2(rcp_approx(dot.x), rcp_approx(dot.y)));
-    const float2 s2 = __fmul2_rn(t, t);
-    float2 p = __ffma2_rn(s2, f2(-1.0f / 11.0f), f2(1.0f / 9.0f));
-    p = __ffma2_rn(s2, p, f2(-1.0f / 7.0f));
-    p = __ffma2_rn(s2, p, f2(1.0f / 5.0f));
-    p = __ffma2_rn(s2, p, f2(-1.0f / 3.0f));
-    const float2 at = __ffma2_rn(__fmul2_rn(t, s2), p, t);
-    const float2 cr = __fadd2_rn(__ffma2_rn(at, f2(a.inv_da), make_float2(gA1.z, gB1.z)), make_float2(gA1.y, gB1.y));
-    const float2 yv = __fadd2_rd(cr, f2(12582912.0f));  // 1.5 * 2^23 + floor(cr), |cr| < 2^22
-    g.ci0 = __float_as_int(yv.x) - 0x4B400000;
-    g.ci1 = __float_as_int(yv.y) - 0x4B400000;
-    g.fc = __ffma2_rn(__fadd2_rn(yv, f2(-12582912.0f)), m1, cr);
-    const float2 v = __fadd2_rn(vr, dv), u = __fadd2_rn(ur, du);
-    g.inv_v = make_float2(rcp_approx(v.x), rcp_approx(v.y));
-    const float2 M = __fmul2_rn(f2(a.D), make_float2(rsqrtf(fmaf(u.x, u.x, v.x * v.x)), rsqrtf(fmaf(u.y, u.y, v.y * v.y))));
-    const float2 kf = make_float2(kfA, kfA + 1.0f);
-    const float2 zr = __fadd2_rn(__ffma2_rn(f2(-a.hdl), kf, f2(zb)), __ffma2_rn(f2(-a.hdl_lo), kf, f2(zb_lo)));
-    g.ur0 = __ffma2_rn(__ffma2_rn(M, zr, f2(-a.w0row)), f2(a.inv_dw), f2(1.0f));  // staged row 0 = detector row -1
-    g.dur = __fmul2_rn(M, f2(a.dz_over_dw));
-}
-
 // RANGED: the launch takes a share of the views (BPArgs k_lo .. acc_final); the plain form
 // compiles without that bookkeeping.
 // PARTIAL: the launch's last z tile holds fewer than B2_T slices.  Its missing slices take every view
@@ -500,7 +154,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     // per-slice view windows; weights omega(k) = sat(k - lo_t) * sat(hi_t - k) relative to kbase
     int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
     float lo[B2_T], hi[B2_T];
-    float2 acc2[B2_T / 2];
+    float2 acc2[1][B2_T / 2];
     {
         int ka[B2_T], kb[B2_T];
         float wa[B2_T], wb[B2_T];
@@ -531,7 +185,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
         }
         const int kbase = active ? kmin : 0;
 #pragma unroll
-        for (int t = 0; t < B2_T / 2; ++t) acc2[t] = make_float2(0.0f, 0.0f);
+        for (int t = 0; t < B2_T / 2; ++t) acc2[0][t] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int t = 0; t < B2_T; ++t) {
             if (ka[t] <= kb[t]) {
@@ -575,7 +229,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
             const int s = s0 + t;
             if (s < a.s_end) {
                 const float v = a.vol[((int64_t)s * a.ny + iy) * a.nx + ix];
-                if (t & 1) acc2[t >> 1].y = v; else acc2[t >> 1].x = v;
+                if (t & 1) acc2[0][t >> 1].y = v; else acc2[0][t >> 1].x = v;
             }
         }
     }
@@ -684,14 +338,17 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
                 // still opening (no slice ended) or closing (every slice started); a plan
                 // without monotone windows has an empty full range (every view general)
                 if (k > kfull_lo && k < kfull_hi)
-                    bp_view<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+                    bp_view<PITCH, MODE, false, !ROWS_OK, B2_T>(smem, colx, fc, ur0, dur, 0.0f, rmax, inv_v, kf, lo,
+                                                                hi, acc2);
                 else if (k < kfull_hi)
-                    bp_view_ramp<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+                    bp_view_ramp<PITCH, MODE, true, !ROWS_OK, B2_T>(smem, colx, fc, ur0, dur, 0.0f, rmax, inv_v, kf,
+                                                                    lo, hi, acc2);
                 else if (k > kfull_lo)
-                    bp_view_ramp<PITCH, MODE, false, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi,
-                                                               acc2);
+                    bp_view_ramp<PITCH, MODE, false, !ROWS_OK, B2_T>(smem, colx, fc, ur0, dur, 0.0f, rmax, inv_v, kf,
+                                                                     lo, hi, acc2);
                 else
-                    bp_view<PITCH, MODE, true, !ROWS_OK>(smem, colx, fc, ur0, dur, rmax, inv_v, kf, lo, hi, acc2);
+                    bp_view<PITCH, MODE, true, !ROWS_OK, B2_T>(smem, colx, fc, ur0, dur, 0.0f, rmax, inv_v, kf, lo,
+                                                               hi, acc2);
             }
         }
         __syncwarp();
@@ -706,248 +363,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     for (int t = 0; t < B2_T; ++t) {
         const int s = s0 + t;
         if (s < a.s_end) {
-            const float v = (t & 1) ? acc2[t >> 1].y : acc2[t >> 1].x;
+            const float v = (t & 1) ? acc2[0][t >> 1].y : acc2[0][t >> 1].x;
             a.vol[((int64_t)s * a.ny + iy) * a.nx + ix] = (!RANGED || a.acc_final) ? v * p.out_scale : v;
         }
-    }
-}
-
-// Geometry of one view for one voxel column (the scalar form of view_geo2).
-struct ViewGeo1 {
-    float fc, ur0, dur, inv_v;
-    int ci;
-};
-
-__device__ __forceinline__ void view_geo1(const BPArgs &a, float ox, float oy, float2 cs, float4 g0, float4 g1,
-                                          float zb, float zb_lo, float kf, ViewGeo1 &g)
-{
-    const float du = fmaf(-ox, cs.y, fmaf(oy, cs.x, g0.z));
-    const float dv = fmaf(-ox, cs.x, fmaf(-oy, cs.y, g0.w));
-    const float cross = fmaf(du, g0.y, dv * -g0.x);
-    const float dot = fmaf(g0.x, du, fmaf(g0.y, dv, g1.x));
-    const float cr = fmaf(atan_small(cross * rcp_approx(dot)), a.inv_da, g1.z) + g1.y;
-    const float yv = __fadd_rd(cr, 12582912.0f);  // 1.5 * 2^23 + floor(cr)
-    g.ci = __float_as_int(yv) - 0x4B400000;
-    g.fc = cr - (yv - 12582912.0f);
-    const float v = g0.y + dv, u = g0.x + du;
-    g.inv_v = rcp_approx(v);
-    const float M = a.D * rsqrtf(fmaf(u, u, v * v));
-    const float zr = fmaf(-a.hdl, kf, zb) + fmaf(-a.hdl_lo, kf, zb_lo);
-    g.ur0 = fmaf(fmaf(M, zr, -a.w0row), a.inv_dw, 1.0f);  // staged row 0 = detector row -1
-    g.dur = M * a.dz_over_dw;
-}
-
-// Work items of a paired launch: A slices [s0, s0 + cnt) and B slices [s0 + N, s0 + N + cnt), cnt <= T
-// (cnt < T only in a PARTIAL launch).
-constexpr int kMaxPairItems = 64;
-struct PairItems {
-    int n;
-    int s0[kMaxPairItems];
-    int cnt[kMaxPairItems];
-};
-
-// Paired-pitch backprojection.  A CTA owns B2_TX x B2_TY columns and two groups of T slices one pitch
-// apart (A at s0, B at s0 + N).  By the periodicity of Sec. II a B slice's PI window is its A
-// slice's one turn later, and at view k + views_per_turn it sees the same alpha*, v*, w* as the A
-// slice at view k; so a thread computes each view's geometry, window classification and end
-// weights once for both groups, and only the taps differ: the producer stages view k (for A) and
-// view k + views_per_turn (for B) with the same column window into a slot pair, one view per
-// consumer iteration.  Ring of RP slot pairs; everything else as k_backproject_tma.
-// Staged rows a paired slot holds (fp32: n_rows + 3, row pairs: n_rows + 2): the slots have a fixed
-// size of PITCH x kPairRows floats, so the B window's offset is a compile-time constant.
-constexpr int kPairRows = 72;
-
-// PARTIAL: items with fewer than T slices per group; the missing slices take every view with clamped
-// rows and are not stored (as in k_backproject_tma's PARTIAL form); launched with ROWS_OK false.
-template <int PITCH, int MODE, bool ROWS_OK, int T, int RP, bool PARTIAL = false>
-__global__ void __launch_bounds__(B2_THREADS, 2)
-    k_backproject_pair(const __grid_constant__ CUtensorMap gmap, BP2Args p, const __grid_constant__ PairItems it)
-{
-    static_assert(!PARTIAL || !ROWS_OK, "missing slices read clamped rows");
-    constexpr int SLOT = PITCH * kPairRows;
-    static_assert(SLOT % 32 == 0, "slots start on 128-byte boundaries (TMA destinations)");
-    extern __shared__ __align__(128) float smem[];
-    // a backprojection launch that follows this one on the stream (other slices, same inputs) may
-    // start its CTAs while this grid's last wave drains
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    __shared__ __align__(8) uint64_t s_full[RP], s_empty[RP];
-    __shared__ float4 s_geo[RP][2];  // the view's table rows (tile reference ray, window start)
-    __shared__ float2 s_cs[RP];      // its (cos, sin)
-    __shared__ int s_K0, s_K1;
-    const BPArgs &a = p.a;
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const bool producer = warp == B2_CW;
-    const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
-    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
-    const int s0 = it.s0[blockIdx.z], cnt = PARTIAL ? it.cnt[blockIdx.z] : T;
-    const bool active = !producer && ix < a.nx && iy < a.ny;
-    const int base = (int)(((128u - (smem_addr(smem) & 127u)) & 127u) >> 2);
-
-    // per-slice view windows of the A group (the B group's are one turn later)
-    int kmin = INT32_MAX, kmax = INT32_MIN, kfull_lo = INT32_MIN, kfull_hi = INT32_MAX;
-    float lo[T], hi[T];
-    float2 accA[T / 2], accB[T / 2];
-    {
-        int ka[T], kb[T];
-        float wa[T], wb[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int s = s0 + t;
-            ka[t] = INT32_MAX;
-            kb[t] = INT32_MIN;
-            wa[t] = wb[t] = 0.0f;
-            if (active && t < cnt) {
-                const int j = s % a.N, m = s / a.N;
-                const int64_t o = ((int64_t)j * a.ny + iy) * a.nx + ix;
-                ka[t] = a.k0[o] + m * a.vpt;
-                kb[t] = a.k1[o] + m * a.vpt;
-                wa[t] = a.w0[o];
-                wb[t] = a.w1[o];
-                kmin = min(kmin, ka[t]);
-                kmax = max(kmax, kb[t]);
-            }
-            if (!(PARTIAL && active && t >= cnt)) {
-                kfull_lo = max(kfull_lo, ka[t]);
-                kfull_hi = min(kfull_hi, kb[t]);
-            }
-        }
-        if (!p.mono) {
-            kfull_lo = INT32_MAX;
-            kfull_hi = INT32_MIN;
-        }
-        const int kbase = active ? kmin : 0;
-#pragma unroll
-        for (int t = 0; t < T / 2; ++t) accA[t] = accB[t] = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const bool missing = PARTIAL && t >= cnt;  // open in every view, not stored
-            lo[t] = missing ? -3.0e9f : (float)(ka[t] - kbase) - wa[t];
-            hi[t] = missing ? 3.0e9f : (float)(kb[t] - kbase) + wb[t];
-        }
-    }
-    if (tid == 0) {
-        s_K0 = INT32_MAX;
-        s_K1 = INT32_MIN;
-        for (int r = 0; r < RP; ++r) {
-            mbar_init(&s_full[r], 1);
-            mbar_init(&s_empty[r], B2_CW);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (active) {
-        atomicMin(&s_K0, kmin);
-        atomicMax(&s_K1, kmax);
-    }
-    __syncthreads();
-    const int K0 = s_K0, K1 = s_K1;
-    if (K0 > K1) return;  // uniform: no column of the tile in the volume
-    const int nviews = K1 - K0 + 1;
-
-    if (producer) {
-        const float4 *geo_t = p.geo + (size_t)(blockIdx.y * p.geo_ntx + blockIdx.x) * a.vpt * 2;
-        const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
-        const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
-        int ps = 0, issued = 0;
-        uint32_t phase = 0;
-        int kmod = ((K0 % a.vpt) + a.vpt) % a.vpt;
-        bool ok = true;
-        float4 g0, g1;
-        float2 cs;
-        if (lane == 0) {
-            g0 = __ldg(geo_t + 2 * kmod);
-            g1 = __ldg(geo_t + 2 * kmod + 1);
-            cs = __ldg(a.trig + kmod);
-        }
-        for (int j = 0; j < nviews; ++j) {
-#ifdef KATS_DEBUG_CHECKS
-            if (g_debug_stall_pairs >= 0 && j >= g_debug_stall_pairs) break;  // test hook: stop issuing
-#endif
-            if (j >= RP && !mbar_wait(&s_empty[ps], phase ^ 1u)) {
-                ok = false;
-                break;
-            }
-            if (lane == 0) {
-                s_geo[ps][0] = g0;
-                s_geo[ps][1] = g1;
-                s_cs[ps] = cs;
-                mbar_arrive_expect_tx(&s_full[ps], 2 * box_bytes);
-                const int clo = __float_as_int(g1.w), kv = K0 + j - (int)a.first_view;
-                tma_load_3d(dst0 + 4u * (uint32_t)(2 * ps * SLOT), &gmap, &s_full[ps], clo, MODE == 0 ? -1 : 0, kv);
-                tma_load_3d(dst0 + 4u * (uint32_t)((2 * ps + 1) * SLOT), &gmap, &s_full[ps], clo, MODE == 0 ? -1 : 0,
-                            kv + a.vpt);
-                kmod = kmod + 1 == a.vpt ? 0 : kmod + 1;
-                if (j + 1 < nviews) {
-                    g0 = __ldg(geo_t + 2 * kmod);
-                    g1 = __ldg(geo_t + 2 * kmod + 1);
-                    cs = __ldg(a.trig + kmod);
-                }
-            }
-            __syncwarp();
-            issued = j + 1;
-            if (++ps == RP) {
-                ps = 0;
-                phase ^= 1u;
-            }
-        }
-        if (lane == 0) {
-            bool landed = true;
-            for (int i = max(0, issued - RP); i < issued; ++i)
-                landed = mbar_wait(&s_full[i % RP], (uint32_t)((i / RP) & 1)) && landed;
-            if (!ok || !landed) atomicExch(p.status, kDevStatusTimeout);
-        }
-        return;
-    }
-
-    const float ox = ((float)tx - 0.5f * (B2_TX - 1)) * a.dx, oy = ((float)ty - 0.5f * (B2_TY - 1)) * a.dy;
-    const int kbase = active ? kmin : 0;
-    float zb, zb_lo;
-    z_base(a, s0, kbase, &zb, &zb_lo);
-    const float rmax = (float)(a.n_rows + 1);
-    constexpr int SH = PITCH == 32 ? 5 : (PITCH == 64 ? 6 : 7);
-    int ps = 0;
-    uint32_t phase = 0;
-    for (int j = 0; j < nviews; ++j) {
-        const int k = K0 + j;
-        if (!__all_sync(0xffffffffu, mbar_wait(&s_full[ps], phase))) {
-            if (lane == 0) atomicExch(p.status, kDevStatusTimeout);
-            return;
-        }
-        if (active && k >= kmin && k <= kmax) {
-            const float kf = (float)(k - kbase);
-            ViewGeo1 g;
-            view_geo1(a, ox, oy, s_cs[ps], s_geo[ps][0], s_geo[ps][1], zb, zb_lo, kf, g);
-            KATS_DCHECK(g.ci >= 0 && g.ci <= p.W - 2, 1);
-            const uint32_t colx = (uint32_t)(base + 2 * ps * SLOT + min(max(g.ci, 0), p.W - 2)) - (0x4B000000u << SH);
-            if (k > kfull_lo && k < kfull_hi)
-                bp_view<PITCH, MODE, false, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf, lo,
-                                                               hi, accA, accB);
-            else if (k < kfull_hi)
-                bp_view_ramp<PITCH, MODE, true, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf,
-                                                                   lo, hi, accA, accB);
-            else if (k > kfull_lo)
-                bp_view_ramp<PITCH, MODE, false, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf,
-                                                                    lo, hi, accA, accB);
-            else
-                bp_view<PITCH, MODE, true, !ROWS_OK, T, SLOT>(smem, colx, g.fc, g.ur0, g.dur, rmax, g.inv_v, kf, lo,
-                                                              hi, accA, accB);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[ps]);
-        if (++ps == RP) {
-            ps = 0;
-            phase ^= 1u;
-        }
-    }
-    if (!active) return;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        if (PARTIAL && t >= cnt) break;
-        const float va = (t & 1) ? accA[t >> 1].y : accA[t >> 1].x;
-        const float vb = (t & 1) ? accB[t >> 1].y : accB[t >> 1].x;
-        a.vol[((int64_t)(s0 + t) * a.ny + iy) * a.nx + ix] = va * p.out_scale;
-        a.vol[((int64_t)(s0 + a.N + t) * a.ny + iy) * a.nx + ix] = vb * p.out_scale;
     }
 }
 
@@ -1004,24 +422,6 @@ static BPArgs bp_args(const Plan &p)
     return a;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)ptr;
-    });
-    return fn;
-}
 
 // Checked build only: columns taken off every staged window, so that a test can see the column
 // check fire (the taps stay clamped inside the window, the result is wrong, nothing faults).
@@ -1042,42 +442,6 @@ static int window_cols(const Plan &p)
     const double rf = std::hypot(std::max(xa, xb), std::max(ya, yb));
     const double span = 2.0 * atan(L / (2.0 * (g.R - rf))) / g.d_alpha;
     return ((int)ceil(span) + 8 + 3) / 4 * 4;
-}
-
-// Decomposition of slices [S0, S1) for the paired kernel: from S0 on, blocks of 2N slices whose
-// first L <= N slices pair with the slices N further on.  A block's L pairs go in items of T slices,
-// T of the instantiated 14 and 12 whichever leaves fewer idle slots (the larger on a tie), the last
-// item partial when T does not divide L; the slices without a partner are ranges for the single
-// kernel.  False when the launch holds no pair.
-struct PairItem {
-    int T, s0, cnt;
-};
-struct PairPlan {
-    std::vector<PairItem> items;
-    std::vector<std::pair<int, int>> rest;  // unpaired slice ranges [s, e)
-};
-
-static bool pair_plan(int S0, int S1, int N, PairPlan *out)
-{
-    PairPlan pp;
-    auto add_rest = [&](int s, int e) {
-        if (e <= s) return;
-        if (!pp.rest.empty() && pp.rest.back().second == s)
-            pp.rest.back().second = e;
-        else
-            pp.rest.push_back({s, e});
-    };
-    int a0 = S0;
-    for (; a0 + N < S1; a0 += 2 * N) {
-        const int L = std::min(N, S1 - a0 - N);
-        const int T = 12 * (int)ceil_div(L, 12) < 14 * (int)ceil_div(L, 14) ? 12 : 14;
-        for (int i = 0; i < L; i += T) pp.items.push_back({T, a0 + i, std::min(T, L - i)});
-        add_rest(a0 + L, a0 + N);
-    }
-    add_rest(a0, S1);
-    if (pp.items.empty()) return false;
-    *out = pp;
-    return true;
 }
 
 template <int PITCH, int MODE, int RP>
@@ -1172,40 +536,20 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
         }
         return KATS_OK;
     };
-    // Slices one pitch apart share their views' geometry (Sec. II periodicity): where a launch holds
-    // such pairs and takes every view, the paired kernel reconstructs them together, T slices of each
-    // per thread, and the rest go through the single kernel.
-    PairPlan pp;
-    const size_t pair_smem = sizeof(float) * (size_t)PITCH * kPairRows * 2 * 3 + 128;  // 3 slot pairs
-    if (!ranged && PITCH <= 64 && srows <= kPairRows && pair_smem <= kTwoPerSm &&
-        pair_plan(a.s_begin, a.s_end, (int)p.N, &pp)) {
-        // one launch per (T, full or partial) group of items
-        for (int T : {14, 12})
-            for (int partial = 0; partial < 2; ++partial) {
-                std::vector<PairItem> grp;
-                for (const PairItem &i : pp.items)
-                    if (i.T == T && (i.cnt < T) == (partial != 0)) grp.push_back(i);
-                if (grp.empty()) continue;
-                auto pk = partial ? (T == 12 ? k_backproject_pair<PITCH, MODE, false, 12, 3, true>
-                                             : k_backproject_pair<PITCH, MODE, false, 14, 3, true>)
-                                  : (T == 12 ? (rows_ok ? k_backproject_pair<PITCH, MODE, true, 12, 3>
-                                                        : k_backproject_pair<PITCH, MODE, false, 12, 3>)
-                                             : (rows_ok ? k_backproject_pair<PITCH, MODE, true, 14, 3>
-                                                        : k_backproject_pair<PITCH, MODE, false, 14, 3>));
-                KATS_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem));
-                for (size_t i0 = 0; i0 < grp.size(); i0 += kMaxPairItems) {
-                    PairItems it;
-                    it.n = (int)std::min<size_t>(kMaxPairItems, grp.size() - i0);
-                    for (int i = 0; i < it.n; ++i) {
-                        it.s0[i] = grp[i0 + (size_t)i].s0;
-                        it.cnt[i] = grp[i0 + (size_t)i].cnt;
-                    }
-                    KATS_CUDA(launch(pk, dim3(gx, gy, (unsigned)it.n), pair_smem, map, b, it));
-                    count_launches(1);
-                    KATS_CUDA(cudaGetLastError());
-                }
-            }
-        for (const auto &r : pp.rest) {
+    // Slices one or more pitches apart share their views' geometry (Sec. II periodicity): where a
+    // launch holds such slices and takes every view, k_backproject_multi reconstructs them together
+    // and the rest go through the single kernel.
+    bool multi = false;
+    std::vector<std::pair<int, int>> rest;
+    if (!ranged) {
+        BP2Args bm = b;
+        bm.srows = srows;
+        int rc = launch_multi<MODE>(p, bm, gF, MultiLaunch{a.s_begin, a.s_end, rows_ok}, st, &n_launched, &rest,
+                                    &multi);
+        if (rc) return rc;
+    }
+    if (multi) {
+        for (const auto &r : rest) {
             int rc = single(r.first, r.second);
             if (rc) return rc;
         }
@@ -1710,6 +1054,8 @@ int katsevich_debug_wait_limit(int polls)
 #ifdef KATS_DEBUG_CHECKS
     const int v = polls > 0 ? polls : kats::kWaitLimit;
     KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_wait_limit, &v, sizeof(int)));
+    int rc = kats::multi_debug_set(v, INT32_MIN);
+    if (rc) return rc;
 #else
     (void)polls;
 #endif
@@ -1721,6 +1067,8 @@ int katsevich_debug_stall_producer(int pairs)
 #ifdef KATS_DEBUG_CHECKS
     const int v = pairs >= 0 ? pairs : -1;
     KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_stall_pairs, &v, sizeof(int)));
+    int rc = kats::multi_debug_set(0, v);
+    if (rc) return rc;
 #else
     (void)pairs;
 #endif
@@ -1738,7 +1086,10 @@ int katsevich_debug_check_flags(int *flags)
     KATS_CUDA(cudaMemcpyFromSymbol(&v, kats::g_debug_flags, sizeof(int)));
     const int zero = 0;
     KATS_CUDA(cudaMemcpyToSymbol(kats::g_debug_flags, &zero, sizeof(int)));
-    *flags = v;
+    int vm = 0;
+    int rc = kats::multi_debug_take_flags(&vm);
+    if (rc) return rc;
+    *flags = v | vm;
     return KATS_OK;
 }
 

@@ -52,6 +52,18 @@ def multipitch_case(endpoint_mode=0):
     return cfg, g, sino.astype(np.float32)
 
 
+def fourpitch_case():
+    """Config-1 scanner (58 slices per pitch) with a 194-slice volume on a ragged 61 x 45 grid:
+    slices 0-19 lead four groups one pitch apart and slices 20-57 three, so the backprojection
+    runs its four- and three-group forms with staged row bands, both with a partial last item."""
+    cfg = dict(synth.config(1))
+    cfg.update(nx=61, ny=45, nz=194, turns=6)
+    g = oracle.derive_geometry(cfg)
+    ell = synth.phantom_for(dict(cfg, phantom="shepp_style"), g, 78)
+    sino = synth.project(g, ell)
+    return cfg, g, sino.astype(np.float32)
+
+
 def odd_case():
     """Small geometry exercising every offset and parity: odd sizes, non-zero
     lambda0 / z0 / lambda_first / alpha and w offsets, odd n_psi, an axis voxel."""

@@ -56,6 +56,8 @@ run("odd", g, sino)
 for mode in (0, 1):
     _, g, sino = cases.multipitch_case(mode)
     run(f"multipitch{mode}", g, sino)
+_, g, sino = cases.fourpitch_case()
+run("fourpitch", g, sino, ("fp32", "fp16", "bf16"))
 _, g, sino = cases.narrow_case()
 run("narrow", g, sino)
 _, g = cases.c3_small_case()
@@ -66,6 +68,11 @@ g = kats.make_geometry(cfg)
 kp0 = kats.Plan(g)
 run("c2_column", g, np.random.default_rng(7).standard_normal(kp0.sino_shape).astype(np.float32),
     ("fp32", "fp16"), host=True)
+# the clinical volume: every slice in a four- or three-group item, each view staged as a row band
+g = kats.make_geometry(synth.config(2))
+kp0 = kats.Plan(g)
+run("c2_full", g, np.random.default_rng(10).standard_normal(kp0.sino_shape).astype(np.float32), ("fp32", "bf16"))
+del kp0
 # the column check is live: a window 16 columns too narrow must trip it (taps stay clamped)
 _, g, sino = cases.c1_case()
 kp = kats.Plan(g)
@@ -100,7 +107,7 @@ def test_checked_build_invariants_and_identity(tmp_path):
     assert checked["narrowed"] & 1 and checked["narrowed"] & 4  # backprojection and adjoint column checks
     assert plain["narrowed"] == 0
     names = sorted(os.listdir(dc))
-    assert names == sorted(os.listdir(dp)) and len(names) >= 14
+    assert names == sorted(os.listdir(dp)) and len(names) >= 20
     for n in names:
         a, b = np.load(dc / n), np.load(dp / n)
         if "adjoint" in n:  # window drains add with global float atomics: order varies run to run

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import c1_case, check32, multipitch_case, narrow_case, near_tie, odd_case, rel_l2, rows80_case, tall_case
+from cases import c1_case, check32, fourpitch_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2, rows80_case, tall_case
 
 pytestmark = pytest.mark.gpu
 
@@ -153,6 +153,23 @@ def test_multipitch_ragged(kats, torch, mode):
     y = np.random.default_rng(1).normal(size=kp.vol_shape).astype(np.float32)
     got = kp.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     check32(got, op.adjoint(y.astype(np.float64)))
+
+
+def test_fourpitch_bands(kats, torch):
+    """Four and three slice groups one pitch apart per thread, each view staged as a band of rows
+    (fp32 against the oracle at the FP32 bar, the 16-bit forms at theirs), and the same volume
+    from slab launches that group the slices differently."""
+    _, g, sino = fourpitch_case()
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    want = op.recon(sino.astype(np.float64))
+    dsino = torch.from_numpy(sino).cuda()
+    vol = kp.recon(dsino).cpu().numpy()
+    check32(vol, want)
+    for p in (kats.KATS_PREC_FP16, kats.KATS_PREC_BF16):
+        assert rel_l2(kp.recon(dsino, precision=p).cpu().numpy(), want) < 1e-3
+    # slices [48, 194): leading slices 48-77 take three groups and 78-105 two, a different grouping
+    slab = kp.recon_slab(dsino.clone(), 0, 48, 194).cpu().numpy()
+    check32(slab, want[48:], name="slab 48-194")
 
 
 def test_odd_geometry_batch(kats, torch):
