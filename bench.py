@@ -365,7 +365,7 @@ def run_ours(args):
         tex32 = kats.native.katsevich_tex_bilinear_rate(False)
         tex16 = kats.native.katsevich_tex_bilinear_rate(True)
         updates_per_s = info["update_count"] / (t_bp / 1e3)
-        roofline = {"kernel": "backprojection (k_backproject_pair + k_backproject_tma, one reconstruction's launches)",
+        roofline = {"kernel": "backprojection (k_backproject_multi + k_backproject_tma, one reconstruction's launches)",
                     "bound": "alu", "achieved": achieved, "peak": smem_peak,
                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": captured_traffic("backprojection"),
                     "peak_source": f"shared-memory data path: 148 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk_kind} clock)",

@@ -132,23 +132,16 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     // slabs of whole 16-slice z tiles.  The first four are small: the first starts backprojecting
     // after a few chunks, and each further 16 slices need only about a chunk more of views, which
     // arrive faster than a small slab is backprojected, so the GPU is not left waiting for the
-    // copies.  Then, where the volume holds them, 2N slices in one slab, whose halves the paired
-    // kernel reconstructs together (its views have arrived by the time the small slabs are done);
-    // the rest in slabs of up to 128 slices, the last 16 (little to copy back at the end).
-    // Measured on the clinical workload: 16 x 4, 140, 36, 16 in 43.1 ms against 44.1 ms for 16 x 4,
-    // 128, 48, 16.
+    // copies.  Then one slab up to 32 slices below the top, whose slices one and two pitches apart
+    // the multi-pitch kernel reconstructs together, and the last 32 (little to copy back at the
+    // end).  Measured on the clinical workload: 16 x 4, 160, 32 in 43.1 ms; 16 x 4, 140, 36, 16 in
+    // 43.8 ms; 16 x 4, 192 in 45.8 ms (the large slab waits for the last views and its copy back
+    // is not hidden); 16 x 3, 208 in 47.3 ms.
     std::vector<int> slab_lo{0};
-    const int64_t pair_slab = 2 * p.N;
     while (slab_lo.back() < nz) {
         const int64_t s0 = slab_lo.back(), left = nz - s0;
-        int64_t n;
-        if (s0 < 64)
-            n = 16;
-        else if (left >= pair_slab + 16 && s0 < 64 + pair_slab)
-            n = pair_slab;
-        else
-            n = left <= 144 ? (left > 32 ? left - 16 : left) : 128;
-        slab_lo.push_back((int)std::min<int64_t>(nz, s0 + std::max<int64_t>(n, 1)));
+        const int64_t n = s0 < 64 ? 16 : (left > 64 ? (left - 32) / 16 * 16 : left);
+        slab_lo.push_back((int)std::min<int64_t>(nz, s0 + n));
     }
     const int n_slabs = (int)slab_lo.size() - 1;
     auto chunk_lo = [&](int i) { return nf * i / n_chunks; };

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 struct Form {
     int G, T, HS;
 };
-constexpr Form kBandForms[] = {{4, 8, 24}, {3, 10, 32}, {3, 8, 24}, {2, 14, 40}, {2, 12, 40}};
+constexpr Form kBandForms[] = {{4, 8, 24}, {4, 6, 24}, {3, 10, 32}, {3, 8, 24}, {2, 14, 40}, {2, 12, 40}};
 constexpr Form kFullForms[] = {{2, 14, kFullRows}, {2, 12, kFullRows}};
 
 // Height in rows of the band that holds every tap of T consecutive slices of one tile at one view,
@@ -322,9 +322,9 @@ struct MultiItem {
 // Decomposition of slices [S0, S1): slice S0 + i (i < N) leads the groups S0 + i + m N below S1.
 // Runs of leading slices with the same number of groups g split into parts of at most gmax groups
 // (as even as possible); a part of two or more groups goes into items of T slices (of the forms
-// available for its group count, the T that leaves the least work, the larger on a tie; the last
-// item partial when T does not divide the run), a part of one group into the single kernel's
-// ranges.
+// available for its group count, the T that leaves the least work, the larger on a tie), the
+// run's remainder into one item of the smallest form that holds it (partial when it is larger), a
+// part of one group into the single kernel's ranges.
 static void multi_plan(int S0, int S1, int N, int gmax, const std::vector<std::vector<int>> &Ts,
                        std::vector<MultiItem> *items, std::vector<std::pair<int, int>> *rest)
 {
@@ -340,11 +340,19 @@ static void multi_plan(int S0, int S1, int N, int gmax, const std::vector<std::v
             const int gc = g / parts + (q < g % parts ? 1 : 0);
             const int a0 = sa + m0 * N;
             if (gc >= 2 && !Ts[gc].empty()) {
-                auto work = [&](int T) { return (L + T - 1) / T * T; };  // slices the items hold
+                // the form for a remainder of r slices, and the slices the items of T hold
+                auto tail_of = [&](int r) {
+                    int t = 0;
+                    for (int T : Ts[gc])
+                        if (T >= r && (!t || T < t)) t = T;
+                    return r ? t : 0;
+                };
+                auto work = [&](int T) { return L / T * T + tail_of(L % T); };
                 int best = Ts[gc][0];
                 for (int T : Ts[gc])
                     if (work(T) < work(best) || (work(T) == work(best) && T > best)) best = T;
-                for (int i = 0; i < L; i += best) items->push_back({gc, best, a0 + i, std::min(best, L - i)});
+                for (int i = 0; i + best <= L; i += best) items->push_back({gc, best, a0 + i, best});
+                if (L % best) items->push_back({gc, tail_of(L % best), a0 + L - L % best, L % best});
             } else {
                 for (int m = 0; m < gc; ++m) rest->push_back({a0 + m * N, a0 + m * N + L});
             }
@@ -386,6 +394,7 @@ static MultiKernel select_multi(const Form &f, bool rows_ok, bool partial, size_
         return pick<MODE, g, t, hs>(rows_ok, partial);             \
     }
     KATS_MULTI_FORM(4, 8, 24)
+    KATS_MULTI_FORM(4, 6, 24)
     KATS_MULTI_FORM(3, 10, 32)
     KATS_MULTI_FORM(3, 8, 24)
     KATS_MULTI_FORM(2, 14, 40)
@@ -394,6 +403,18 @@ static MultiKernel select_multi(const Form &f, bool rows_ok, bool partial, size_
     KATS_MULTI_FORM(2, 12, kFullRows)
 #undef KATS_MULTI_FORM
     return nullptr;
+}
+
+// The T values per group count of a set of forms (index G).
+std::vector<std::vector<int>> forms_T(const std::vector<Form> &forms, int *gmax)
+{
+    std::vector<std::vector<int>> Ts(5);
+    *gmax = 1;
+    for (const Form &f : forms) {
+        Ts[f.G].push_back(f.T);
+        *gmax = std::max(*gmax, f.G);
+    }
+    return Ts;
 }
 
 }  // namespace
@@ -416,12 +437,8 @@ int launch_multi(const Plan &p, const BP2Args &b0, const void *gF, const MultiLa
     for (const Form &f : forms) have2 |= f.G == 2;
     if (!have2)
         for (const Form &f : kFullForms) forms.push_back(f);
-    std::vector<std::vector<int>> Ts(5);
     int gmax = 1;
-    for (const Form &f : forms) {
-        Ts[f.G].push_back(f.T);
-        gmax = std::max(gmax, f.G);
-    }
+    const std::vector<std::vector<int>> Ts = forms_T(forms, &gmax);
     std::vector<MultiItem> items;
     std::vector<std::pair<int, int>> rst;
     multi_plan(ml.s_begin, ml.s_end, (int)p.N, gmax, Ts, &items, &rst);
@@ -515,3 +532,41 @@ int multi_debug_take_flags(int *flags)
 }
 
 }  // namespace kats
+
+extern "C" int katsevich_slice_groups(int64_t s_begin, int64_t s_end, int64_t slices_per_pitch, int max_groups,
+                                      int32_t *groups, int32_t *t, int32_t *s0, int32_t *cnt, int max_items,
+                                      int *n_items, int32_t *rest, int max_rest, int *n_rest)
+{
+    using namespace kats;
+    if (!groups || !t || !s0 || !cnt || !n_items || !rest || !n_rest || s_begin < 0 || s_end < s_begin ||
+        s_end > INT32_MAX || slices_per_pitch < 1 || slices_per_pitch > INT32_MAX || max_groups < 2 ||
+        max_groups > 4 || max_items < 0 || max_rest < 0) {
+        set_error("bad argument");
+        return KATS_EINVAL;
+    }
+    std::vector<Form> forms;
+    for (const Form &f : kBandForms)
+        if (f.G <= max_groups) forms.push_back(f);
+    int gmax = 1;
+    const std::vector<std::vector<int>> Ts = forms_T(forms, &gmax);
+    std::vector<MultiItem> items;
+    std::vector<std::pair<int, int>> rst;
+    multi_plan((int)s_begin, (int)s_end, (int)slices_per_pitch, gmax, Ts, &items, &rst);
+    *n_items = (int)items.size();
+    *n_rest = (int)rst.size();
+    if ((int)items.size() > max_items || (int)rst.size() > max_rest) {
+        set_error("%zu items and %zu ranges do not fit %d / %d", items.size(), rst.size(), max_items, max_rest);
+        return KATS_ESPACE;
+    }
+    for (size_t i = 0; i < items.size(); ++i) {
+        groups[i] = items[i].G;
+        t[i] = items[i].T;
+        s0[i] = items[i].s0;
+        cnt[i] = items[i].cnt;
+    }
+    for (size_t j = 0; j < rst.size(); ++j) {
+        rest[2 * j] = rst[j].first;
+        rest[2 * j + 1] = rst[j].second;
+    }
+    return KATS_OK;
+}

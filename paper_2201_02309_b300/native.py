@@ -33,7 +33,10 @@ EXPORTS = ["katsevich_fit_pitch", "katsevich_plan", "katsevich_plan_info", "kats
            "katsevich_tex_bilinear_rate",
            "katsevich_launch_count", "katsevich_debug_checks_enabled", "katsevich_debug_check_flags",
            "katsevich_debug_narrow_window", "katsevich_debug_nonmonotone", "katsevich_debug_wait_limit",
-           "katsevich_debug_stall_producer"]
+           "katsevich_debug_stall_producer", "katsevich_slice_groups"]
+
+
+I32P = ctypes.POINTER(ctypes.c_int32)
 
 
 class kats_geometry(ctypes.Structure):
@@ -144,6 +147,9 @@ def load() -> ctypes.CDLL:
         "katsevich_arena_in_use": (ctypes.c_int64, [P]),
         "katsevich_arena_destroy": (None, [P]),
         "katsevich_debug_fail_allocs": (None, [ctypes.c_int]),
+        "katsevich_slice_groups": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                  I32P, I32P, I32P, I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                  I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "katsevich_project": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64, ctypes.c_int64,
                                              P]),
         "katsevich_sparse_upsample": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64,
@@ -390,6 +396,18 @@ def katsevich_arena_destroy(arena: int) -> None:
 
 def katsevich_debug_fail_allocs(n: int) -> None:
     load().katsevich_debug_fail_allocs(n)
+
+
+def katsevich_slice_groups(s_begin: int, s_end: int, slices_per_pitch: int, max_groups: int = 4):
+    """The backprojection's slice grouping (host only): ([(groups, t, s0, cnt), ...], [(s, e), ...])."""
+    cap = 4096
+    arr = [(ctypes.c_int32 * cap)() for _ in range(4)]
+    rest = (ctypes.c_int32 * (2 * cap))()
+    ni, nr = ctypes.c_int(0), ctypes.c_int(0)
+    check(load().katsevich_slice_groups(s_begin, s_end, slices_per_pitch, max_groups, *arr, cap, ctypes.byref(ni),
+                                        rest, cap, ctypes.byref(nr)))
+    items = [tuple(int(a[i]) for a in arr) for i in range(ni.value)]
+    return items, [(int(rest[2 * j]), int(rest[2 * j + 1])) for j in range(nr.value)]
 
 
 # --- data simulation -----------------------------------------------------------

@@ -83,7 +83,7 @@ def odd_case():
 
 def close_paths(a, b, name=""):
     """Two FP32 evaluations of the same operator whose slices were grouped differently (the
-    paired-pitch kernel takes slices s and s + N together where a launch holds both, so a slab
+    multi-pitch kernel takes slices s, s + N, ... together where a launch holds them, so a slab
     launch and a whole-volume launch can group a slice differently): the geometry and end
     weights of a slice are then rounded relative to another reference view, and the results
     agree to FP32 rounding rather than bit for bit.  Bars: rel-L2 <= 2e-6 and every element

@@ -2,7 +2,7 @@
 (one slab per rank, no exchange between them): a slab computed from only the
 sinogram views it reads equals those slices of the whole-volume reconstruction
 (bit for bit where the slab and the whole volume group their slices alike, to FP32
-rounding where the paired-pitch kernel pairs a slice differently), and the views it
+rounding where the multi-pitch kernel groups a slice differently), and the views it
 reads are the union of its voxels' PI windows, taken here from the plan's one-pitch
 k0 / k1 tables shifted by whole turns."""
 import numpy as np
