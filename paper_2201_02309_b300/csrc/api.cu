@@ -107,6 +107,33 @@ static void slab_views(const Plan &p, int64_t s0, int64_t s1, int64_t *lo, int64
 // later chunks are still arriving; each slab of the volume is copied back
 // while later slabs are backprojected.  Work issued on st after this call
 // waits for all of it.
+// Groups of leading slices [la, lb) for the host pipeline's last slab [s0, s1), in launch order:
+// leads s in [s0, s0 + N) head the slices s + mN below s1; runs of leads with the same number of
+// groups in increasing s (the most groups first), the first run split in two halves, so that the
+// last group launched (the fewest groups) has few slices to copy back.  Empty when the slab spans
+// no more than a pitch (no slice has a partner).
+constexpr int kMaxLeadChunks = 8;
+static std::vector<std::pair<int, int>> lead_chunks(int s0, int s1, int N)
+{
+    std::vector<std::pair<int, int>> out;
+    if (s1 - s0 <= N) return out;
+    const int le = std::min(s0 + N, s1);
+    auto groups = [&](int s) { return (s1 - 1 - s) / N + 1; };
+    for (int a = s0; a < le && (int)out.size() < kMaxLeadChunks - 1;) {
+        int b = a + 1;
+        while (b < le && groups(b) == groups(a)) ++b;
+        if (out.empty() && b - a > 1) {
+            out.push_back({a, a + (b - a) / 2});
+            out.push_back({a + (b - a) / 2, b});
+        } else {
+            out.push_back({a, b});
+        }
+        a = b;
+    }
+    out.back().second = le;  // any runs beyond the limit go with the last group
+    return out;
+}
+
 int recon_one_host(const Plan &p, int precision, const float *host_sino, float *host_vol, void *ws, cudaStream_t st)
 {
     kats::NvtxRange nvtx_range("katsevich: host item");
@@ -132,15 +159,19 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     // slabs of whole 16-slice z tiles.  The first four are small: the first starts backprojecting
     // after a few chunks, and each further 16 slices need only about a chunk more of views, which
     // arrive faster than a small slab is backprojected, so the GPU is not left waiting for the
-    // copies.  Then one slab up to 32 slices below the top, whose slices one and two pitches apart
-    // the multi-pitch kernel reconstructs together, and the last 32 (little to copy back at the
-    // end).  Measured on the clinical workload: 16 x 4, 160, 32 in 43.1 ms; 16 x 4, 140, 36, 16 in
-    // 43.8 ms; 16 x 4, 192 in 45.8 ms (the large slab waits for the last views and its copy back
-    // is not hidden); 16 x 3, 208 in 47.3 ms.
+    // copies.  Five of them fill the GPU until the last views have arrived.  Then, where more than
+    // a pitch is left, the rest in one slab whose slices one and more pitches apart the multi-pitch
+    // kernel reconstructs together, launched in groups of leading slices (lead_chunks) so that
+    // each group is copied back while the next one runs; otherwise one slab up to 32 slices below
+    // the top and the last 32.  Measured on the clinical workload (timelines from CUDA events):
+    // 16 x 5 and 176 in leads 80-97, 98-115 (three groups), 116-149 (two) in 42.4 ms; the same
+    // with 80-115 whole in 42.9, with the two-group leads first in 43.6, in one launch in 44.6;
+    // 16 x 4 and 192 in leads 64-115, 116-133 in 43.2, with 116-133 first in 45.4 (36 slices of
+    // two groups, two small launches: 6 ms); 16 x 4, 160, 32 in 43.2.
     std::vector<int> slab_lo{0};
     while (slab_lo.back() < nz) {
         const int64_t s0 = slab_lo.back(), left = nz - s0;
-        const int64_t n = s0 < 64 ? 16 : (left > 64 ? (left - 32) / 16 * 16 : left);
+        const int64_t n = s0 < 80 ? 16 : (left > p.N ? left : (left > 64 ? (left - 32) / 16 * 16 : left));
         slab_lo.push_back((int)std::min<int64_t>(nz, s0 + n));
     }
     const int n_slabs = (int)slab_lo.size() - 1;
@@ -151,16 +182,21 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
     cudaStream_t cs = nullptr, fs = nullptr;
     // events: [0] start, [1, n_chunks] copies, then slabs, then [.. + n_chunks] filter chunks, last: copies done
     std::vector<cudaEvent_t> ev((size_t)(2 * n_chunks + n_slabs + 2), nullptr);
+    std::vector<cudaEvent_t> lev(kMaxLeadChunks, nullptr);  // the last slab's groups of leading slices
     const size_t ev_filt = (size_t)(1 + n_chunks + n_slabs);
     auto cleanup = [&]() {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);  // released once recorded work completes
+        for (cudaEvent_t e : lev)
+            if (e) cudaEventDestroy(e);
         if (cs) cudaStreamDestroy(cs);   // likewise
         if (fs) cudaStreamDestroy(fs);
     };
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking);
     for (size_t i = 0; e == cudaSuccess && i < ev.size(); ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    for (size_t i = 0; e == cudaSuccess && i < lev.size(); ++i)
+        e = cudaEventCreateWithFlags(&lev[i], cudaEventDisableTiming);
     int rc = KATS_OK;
     if (e != cudaSuccess) rc = cuda_fail(e, "copy / filter streams and events");
     // both side streams start after the work already issued on st (e.g. a previous item using ws)
@@ -212,6 +248,28 @@ int recon_one_host(const Plan &p, int precision, const float *host_sino, float *
             // the slab needs every chunk filtered so far (chunks complete in order on fs)
             e = cudaStreamWaitEvent(st, ev[ev_filt + (size_t)(filtered - 1)], 0);
             if (e != cudaSuccess) break;
+            const std::vector<std::pair<int, int>> leads =
+                j == n_slabs - 1 ? lead_chunks(s0, s0 + n, (int)p.N) : std::vector<std::pair<int, int>>();
+            if (!leads.empty()) {
+                // groups of leading slices, each copied back while the next one is backprojected
+                for (size_t q = 0; !rc && e == cudaSuccess && q < leads.size(); ++q) {
+                    BPRange r;
+                    r.lead_end = leads[q].second;
+                    const int la = leads[q].first;
+                    rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, la, s0 + n - la, r)
+                              : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, la, s0 + n - la,
+                                                     r);
+                    if (rc) break;
+                    e = cudaEventRecord(lev[q], st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, lev[q], 0);
+                    for (const auto &sr : lead_ranges(la, s0 + n, (int)p.N, leads[q].second))
+                        if (e == cudaSuccess)
+                            e = cudaMemcpyAsync(host_vol + sr.first * nxy, d_vol + sr.first * nxy,
+                                                sizeof(float) * (size_t)((sr.second - sr.first) * nxy),
+                                                cudaMemcpyDeviceToHost, cs);
+                }
+                continue;
+            }
             rc = fp32 ? launch_backproject(p, (const float *)rws, d_vol, st, s0, n)
                       : launch_backproject16(p, precision, (const uint32_t *)rws, d_vol, st, s0, n);
             if (rc) break;

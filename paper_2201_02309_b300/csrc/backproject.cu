@@ -453,7 +453,8 @@ static auto select_tma(bool ranged, bool rows_ok)
 }
 
 template <int PITCH, int MODE>
-static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched)
+static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched,
+                      int lead_end)
 {
     *launched = false;
     // staged rows: fp32 -> detector rows -1 .. n_rows + 1; row pairs -> pair-rows 0 .. n_rows + 1
@@ -544,8 +545,8 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
     if (!ranged) {
         BP2Args bm = b;
         bm.srows = srows;
-        int rc = launch_multi<MODE>(p, bm, gF, MultiLaunch{a.s_begin, a.s_end, rows_ok}, st, &n_launched, &rest,
-                                    &multi);
+        int rc = launch_multi<MODE>(p, bm, gF, MultiLaunch{a.s_begin, a.s_end, rows_ok, lead_end}, st, &n_launched,
+                                    &rest, &multi);
         if (rc) return rc;
     }
     if (multi) {
@@ -554,19 +555,22 @@ static int launch_tma(const Plan &p, const BPArgs &a, const void *gF, int W, cud
             if (rc) return rc;
         }
     } else {
-        int rc = single(a.s_begin, a.s_end);
-        if (rc) return rc;
+        for (const auto &r : lead_ranges(a.s_begin, a.s_end, (int)p.N, lead_end)) {
+            int rc = single(r.first, r.second);
+            if (rc) return rc;
+        }
     }
     *launched = true;
     return KATS_OK;
 }
 
 template <int MODE>
-static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched)
+static int launch_tma_any(const Plan &p, const BPArgs &a, const void *gF, int W, cudaStream_t st, bool *launched,
+                          int lead_end)
 {
-    if (W <= 32) return launch_tma<32, MODE>(p, a, gF, W, st, launched);
-    if (W <= 64) return launch_tma<64, MODE>(p, a, gF, W, st, launched);
-    if (W <= 128) return launch_tma<128, MODE>(p, a, gF, W, st, launched);
+    if (W <= 32) return launch_tma<32, MODE>(p, a, gF, W, st, launched, lead_end);
+    if (W <= 64) return launch_tma<64, MODE>(p, a, gF, W, st, launched, lead_end);
+    if (W <= 128) return launch_tma<128, MODE>(p, a, gF, W, st, launched, lead_end);
     *launched = false;
     return KATS_OK;
 }
@@ -588,8 +592,13 @@ int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vo
     a.vol = vol;
     bool launched = false;
     const int W = std::max(4, window_cols(p) - g_debug_narrow.load());
-    int rc = prec == KATS_PREC_FP16 ? launch_tma_any<2>(p, a, gFp, W, st, &launched)
-                                    : launch_tma_any<1>(p, a, gFp, W, st, &launched);
+    if (range.lead_end != INT32_MAX && (range.k_lo != INT32_MIN || range.k_hi != INT32_MAX || range.acc_in ||
+                                        !range.acc_final)) {
+        set_error("a launch restricted to leading slices takes every view");
+        return KATS_EINVAL;
+    }
+    int rc = prec == KATS_PREC_FP16 ? launch_tma_any<2>(p, a, gFp, W, st, &launched, range.lead_end)
+                                    : launch_tma_any<1>(p, a, gFp, W, st, &launched, range.lead_end);
     if (rc) return rc;
     if (!launched) {
         set_error("reduced-precision backprojection needs the staged (TMA) kernel; this detector is narrower than "
@@ -616,13 +625,23 @@ int launch_backproject(const Plan &p, const float *gF, float *vol, cudaStream_t 
     a.vol = vol;
     const int W = std::max(4, window_cols(p) - g_debug_narrow.load());
     bool launched = false;
-    int rc = launch_tma_any<0>(p, a, gF, W, st, &launched);
+    if (range.lead_end != INT32_MAX && (range.k_lo != INT32_MIN || range.k_hi != INT32_MAX || range.acc_in ||
+                                        !range.acc_final)) {
+        set_error("a launch restricted to leading slices takes every view");
+        return KATS_EINVAL;
+    }
+    int rc = launch_tma_any<0>(p, a, gF, W, st, &launched, range.lead_end);
     if (rc || launched) return rc;
-    dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
-              (unsigned)ceil_div(a.s_end - a.s_begin, BP_T));
-    k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(a);
-    count_launches(1);
-    KATS_CUDA(cudaGetLastError());
+    for (const auto &r : lead_ranges(a.s_begin, a.s_end, (int)p.N, range.lead_end)) {
+        BPArgs ar = a;
+        ar.s_begin = r.first;
+        ar.s_end = r.second;
+        dim3 grid((unsigned)ceil_div(p.g.nx, BP_BX), (unsigned)ceil_div(p.g.ny, BP_BY),
+                  (unsigned)ceil_div(ar.s_end - ar.s_begin, BP_T));
+        k_backproject<<<grid, dim3(BP_BX, BP_BY), 0, st>>>(ar);
+        count_launches(1);
+        KATS_CUDA(cudaGetLastError());
+    }
     return KATS_OK;
 }
 

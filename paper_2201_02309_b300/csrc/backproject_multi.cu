@@ -326,10 +326,11 @@ struct MultiItem {
 // run's remainder into one item of the smallest form that holds it (partial when it is larger), a
 // part of one group into the single kernel's ranges.
 static void multi_plan(int S0, int S1, int N, int gmax, const std::vector<std::vector<int>> &Ts,
-                       std::vector<MultiItem> *items, std::vector<std::pair<int, int>> *rest)
+                       std::vector<MultiItem> *items, std::vector<std::pair<int, int>> *rest,
+                       int lead_limit = INT32_MAX)
 {
     auto groups = [&](int s) { return (S1 - 1 - s) / N + 1; };
-    const int lead_end = std::min(S0 + N, S1);
+    const int lead_end = std::min(std::min(S0 + N, S1), lead_limit);
     for (int sa = S0; sa < lead_end;) {
         const int g = groups(sa);
         int sb = sa + 1;
@@ -441,7 +442,7 @@ int launch_multi(const Plan &p, const BP2Args &b0, const void *gF, const MultiLa
     const std::vector<std::vector<int>> Ts = forms_T(forms, &gmax);
     std::vector<MultiItem> items;
     std::vector<std::pair<int, int>> rst;
-    multi_plan(ml.s_begin, ml.s_end, (int)p.N, gmax, Ts, &items, &rst);
+    multi_plan(ml.s_begin, ml.s_end, (int)p.N, gmax, Ts, &items, &rst, ml.lead_end);
     if (items.empty()) return KATS_OK;
 
     const dim3 block(B2_THREADS);

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -424,7 +425,9 @@ inline EncodeTiledFn encode_fn()
 struct MultiLaunch {
     int s_begin, s_end;
     bool rows_ok;
+    int lead_end;  // leading slices [s_begin, min(s_begin + N, lead_end)) only (BPRange::lead_end)
 };
+
 
 // Launches the multi-pitch kernel over the slices of ml that have a partner one or more pitches up
 // (each launch after the first of a call with programmatic dependent launch when *n_launched > 0;

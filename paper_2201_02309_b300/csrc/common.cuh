@@ -6,6 +6,8 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "../../include/katsevich.h"
@@ -118,7 +120,21 @@ int launch_filter16(const Plan &p, int prec, const float *sino, uint32_t *gFp, v
 struct BPRange {
     int k_lo = INT32_MIN, k_hi = INT32_MAX;
     int acc_in = 0, acc_final = 1;
+    // lead_end: only the slices s of [s_begin, s_end) whose leading slice s_begin + (s - s_begin)
+    // mod N lies below lead_end (slices one or more pitches apart go together; the host pipeline
+    // copies such a group of leads back while the next one runs); takes every view
+    int lead_end = INT32_MAX;
 };
+// Slices of [s_begin, s_end) whose leading slice s_begin + (s - s_begin) mod N is below lead_end,
+// as ranges.
+inline std::vector<std::pair<int, int>> lead_ranges(int s_begin, int s_end, int N, int lead_end)
+{
+    std::vector<std::pair<int, int>> r;
+    const int le = std::min(lead_end, s_begin + N);
+    for (int b = s_begin; b < s_end; b += N)
+        if (b < std::min(s_end, b + (le - s_begin))) r.push_back({b, std::min(s_end, b + (le - s_begin))});
+    return r;
+}
 // slabs: slices [s_begin, s_begin + s_count), s_begin a multiple of 16 (s_count < 0: every slice)
 int launch_backproject16(const Plan &p, int prec, const uint32_t *gFp, float *vol, cudaStream_t st, int s_begin = 0,
                          int s_count = -1, const BPRange &range = BPRange());
