@@ -10,6 +10,8 @@ child process with libkatsevich_debug.so; nothing here faults, traps or hangs th
 * The general end-weight path for plans whose PI windows are not monotone in z.  With the plan
   treated as non-monotone every view takes that path instead of the ramp walk; the volume must
   be the same bit for bit, and match the oracle.
+Both for the single-group kernel (config-1 case) and for the slice-group kernel (a volume of four
+pitches, where slices one to three pitches apart share a thread).
 """
 import json
 import os
@@ -20,7 +22,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import c1_case, check32
+from cases import c1_case, check32, fourpitch_case
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +81,26 @@ native.katsevich_debug_nonmonotone(0)
 rep["general_equal_ramp"] = bool(np.array_equal(general, clean))
 np.save(f"{out}/general.npy", general)
 np.save(f"{out}/clean.npy", clean)
+
+# the same two paths in the slice-group kernel (four and three groups of slices one pitch apart)
+_, g4, sino4 = cases.fourpitch_case()
+kp4 = kats.Plan(g4)
+d4 = torch.from_numpy(sino4).cuda()
+clean4 = kp4.recon(d4).cpu().numpy()
+native.katsevich_debug_wait_limit(1 << 12)
+native.katsevich_debug_stall_producer(3)
+stalled4 = torch.full(kp4.vol_shape, float("nan"), device="cuda")
+kp4.recon(d4, out=stalled4)
+native.katsevich_debug_stall_producer(-1)
+native.katsevich_debug_wait_limit(0)
+rep["groups_stalled_nan"] = int(torch.isnan(stalled4).sum().item())
+rep["groups_status_stalled"] = native.katsevich_device_status(kp4.handle)
+rep["groups_again_equal_clean"] = bool(np.array_equal(kp4.recon(d4).cpu().numpy(), clean4))
+native.katsevich_debug_nonmonotone(1)
+general4 = kp4.recon(d4).cpu().numpy()
+native.katsevich_debug_nonmonotone(0)
+rep["groups_general_equal_ramp"] = bool(np.array_equal(general4, clean4))
+np.save(f"{out}/general4.npy", general4)
 rep["flags"] = native.katsevich_debug_check_flags()
 print("REPORT " + json.dumps(rep))
 """
@@ -102,7 +124,12 @@ def test_timeout_path_and_general_window_path(tmp_path):
     assert rep["served"] == kats.native.KATS_ETIMEOUT
     assert rep["served_after"] and rep["again_equal_clean"] and rep["status_again"] == 0
     assert rep["general_equal_ramp"]
+    assert rep["groups_status_stalled"] == 1 and rep["groups_stalled_nan"] > 0
+    assert rep["groups_again_equal_clean"] and rep["groups_general_equal_ramp"]
     assert rep["flags"] == 0
     _, g, sino = c1_case()
     want = oracle.Plan(g).recon(sino.astype(np.float64))
     check32(np.load(tmp_path / "general.npy"), want, name="general end-weight path")
+    _, g4, sino4 = fourpitch_case()
+    want4 = oracle.Plan(g4).recon(sino4.astype(np.float64))
+    check32(np.load(tmp_path / "general4.npy"), want4, name="general end-weight path, slice groups")
