@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const int warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == B2_CW;
     const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
-    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    int bx, by;
+    cta_tile(&bx, &by);
+    const int ix = bx * B2_TX + tx, iy = by * B2_TY + ty;
     const int s0 = a.s_begin + blockIdx.z * B2_T;
     const bool active = !producer && ix < a.nx && iy < a.ny;
     // slots start at the first 128-byte boundary of the dynamic shared memory (TMA destinations)
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
 
     if (producer) {
         // ---------------- producer warp: the views' table rows (window start in them) + TMA
-        const float4 *geo_t = p.geo + (size_t)(blockIdx.y * p.geo_ntx + blockIdx.x) * a.vpt * 2;
+        const float4 *geo_t = p.geo + (size_t)(by * p.geo_ntx + bx) * a.vpt * 2;
         const uint32_t box_bytes = (uint32_t)(PITCH * p.srows * 4);
         const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
         int ps = 0, issued = 0;  // pair slot; view pairs issued
@@ -753,7 +755,9 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     __shared__ float s_fmax[BT_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tx = tid % B2_TX, ty = tid / B2_TX;
-    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    int bx, by;
+    cta_tile(&bx, &by);
+    const int ix = bx * B2_TX + tx, iy = by * B2_TY + ty;
     const int s0 = a.s_begin + blockIdx.z * B2_T;
     const bool active = ix < a.nx && iy < a.ny;
 
@@ -829,7 +833,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
 
     // first window column of view k: the plan's table (lowest column touched at the tile corners,
     // one column of slack, 16-byte aligned)
-    const float4 *geo_t = geo + (size_t)(blockIdx.y * geo_ntx + blockIdx.x) * a.vpt * 2;
+    const float4 *geo_t = geo + (size_t)(by * geo_ntx + bx) * a.vpt * 2;
     auto window_col = [&](int k) {
         const int km = ((k % a.vpt) + a.vpt) % a.vpt;
         return __float_as_int(__ldg(geo_t + 2 * km + 1).w);

@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const int warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == B2_CW;
     const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
-    const int ix = blockIdx.x * B2_TX + tx, iy = blockIdx.y * B2_TY + ty;
+    int bx, by;
+    cta_tile(&bx, &by);
+    const int ix = bx * B2_TX + tx, iy = by * B2_TY + ty;
     const int s0 = it.s0[blockIdx.z], cnt = PARTIAL ? it.cnt[blockIdx.z] : T;
     const bool active = !producer && ix < a.nx && iy < a.ny;
     // slots start at the first 128-byte boundary of the dynamic shared memory after the guard
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const int nviews = K1 - K0 + 1;
 
     if (producer) {
-        const float4 *geo_t = p.geo + (size_t)(blockIdx.y * p.geo_ntx + blockIdx.x) * a.vpt * 2;
+        const float4 *geo_t = p.geo + (size_t)(by * p.geo_ntx + bx) * a.vpt * 2;
         const uint32_t box_bytes = (uint32_t)(PITCH * p.box_rows * 4);
         const uint32_t dst0 = smem_addr(smem) + 4u * (uint32_t)base;
         // group 0's lowest slice relative to the source at view K0 + j: z_rel(zb, zb_lo, j)
@@ -472,7 +474,10 @@ int launch_multi(const Plan &p, const BP2Args &b0, const void *gF, const MultiLa
             }
             size_t smem = 0;
             MultiKernel kern = select_multi<MODE>(f, ml.rows_ok, partial != 0, &smem);
-            if (!kern) return KATS_OK;
+            if (!kern) {  // every form in kBandForms / kFullForms is instantiated
+                set_error("multi-pitch backprojection form (%d groups of %d, %d rows) not built", f.G, f.T, f.HS);
+                return KATS_EINVAL;
+            }
             KATS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             for (size_t i0 = 0; i0 < grp.size(); i0 += kMaxMultiItems) {
                 MultiItems it;

@@ -140,6 +140,23 @@ struct BP2Args {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// The staged kernels' column tile of a CTA.  Launch order walks the tile grid in strips of
+// kStripTiles tile columns, row by row within a strip (the last strip narrower when the grid's
+// width is not a multiple), so that the CTAs resident at one time cover a compact patch of the
+// volume: their views' detector columns and rows overlap, and the staged windows are re-read from
+// L2 rather than DRAM (clinical backprojection: DRAM reads 24.5 -> 7.0 GB per reconstruction
+// against row-by-row order; strips of 4, 6 and 16 tiles: 9.2, 8.2 and 9.0 GB).
+constexpr int kStripTiles = 8;
+__device__ __forceinline__ void cta_tile(int *bx, int *by)
+{
+    const int gx = (int)gridDim.x, gy = (int)gridDim.y;
+    const int l = (int)blockIdx.x + gx * (int)blockIdx.y;
+    const int x0 = l / (kStripTiles * gy) * kStripTiles, w = min(kStripTiles, gx - x0);
+    const int r = l - x0 * gy;
+    *bx = x0 + r % w;
+    *by = r / w;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
