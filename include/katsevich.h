@@ -475,15 +475,18 @@ KATS_API int katsevich_debug_stall_producer(int pairs);
  * them.  Item i has groups[i] groups (2 to max_groups, at most 4) of cnt[i] slices each, group m
  * covering slices [s0[i] + m N, s0[i] + m N + cnt[i]), N = slices_per_pitch, in a form with t[i]
  * >= cnt[i] slices per group per thread; slices in no item go to the one-group kernel as ranges
- * [rest[2j], rest[2j + 1]).  Every slice lies in exactly one item group or range.  The library's
+ * [rest[2j], rest[2j + 1]).  lead_end restricts the leading slices to [s_begin, lead_end), and so
+ * the slices to those whose leading slice s_begin + (s - s_begin) mod N lies below it (the host
+ * pipeline launches its last slab in such groups of leads; INT64_MAX: no restriction).  Every
+ * slice of the (restricted) set lies in exactly one item group or range.  The library's
  * own launches use this grouping with max_groups from the plan's row-band bound (4 for the
  * clinical scanners).  Capacities: max_items items, max_rest ranges; the counts go to *n_items and
  * *n_rest in any case.  Errors: KATS_EINVAL for a NULL pointer or bad size, KATS_ESPACE when a
  * capacity is too small.
  */
 KATS_API int katsevich_slice_groups(int64_t s_begin, int64_t s_end, int64_t slices_per_pitch, int max_groups,
-                                    int32_t *groups, int32_t *t, int32_t *s0, int32_t *cnt, int max_items,
-                                    int *n_items, int32_t *rest, int max_rest, int *n_rest);
+                                    int64_t lead_end, int32_t *groups, int32_t *t, int32_t *s0, int32_t *cnt,
+                                    int max_items, int *n_items, int32_t *rest, int max_rest, int *n_rest);
 
 /*
  * Number of kernels the library has launched in this process so far (every

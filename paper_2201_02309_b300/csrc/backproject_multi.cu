@@ -540,8 +540,8 @@ int multi_debug_take_flags(int *flags)
 }  // namespace kats
 
 extern "C" int katsevich_slice_groups(int64_t s_begin, int64_t s_end, int64_t slices_per_pitch, int max_groups,
-                                      int32_t *groups, int32_t *t, int32_t *s0, int32_t *cnt, int max_items,
-                                      int *n_items, int32_t *rest, int max_rest, int *n_rest)
+                                      int64_t lead_end, int32_t *groups, int32_t *t, int32_t *s0, int32_t *cnt,
+                                      int max_items, int *n_items, int32_t *rest, int max_rest, int *n_rest)
 {
     using namespace kats;
     if (!groups || !t || !s0 || !cnt || !n_items || !rest || !n_rest || s_begin < 0 || s_end < s_begin ||
@@ -557,7 +557,8 @@ extern "C" int katsevich_slice_groups(int64_t s_begin, int64_t s_end, int64_t sl
     const std::vector<std::vector<int>> Ts = forms_T(forms, &gmax);
     std::vector<MultiItem> items;
     std::vector<std::pair<int, int>> rst;
-    multi_plan((int)s_begin, (int)s_end, (int)slices_per_pitch, gmax, Ts, &items, &rst);
+    multi_plan((int)s_begin, (int)s_end, (int)slices_per_pitch, gmax, Ts, &items, &rst,
+               (int)std::min<int64_t>(std::max<int64_t>(lead_end, INT32_MIN), INT32_MAX));
     *n_items = (int)items.size();
     *n_rest = (int)rst.size();
     if ((int)items.size() > max_items || (int)rst.size() > max_rest) {

@@ -148,8 +148,9 @@ def load() -> ctypes.CDLL:
         "katsevich_arena_destroy": (None, [P]),
         "katsevich_debug_fail_allocs": (None, [ctypes.c_int]),
         "katsevich_slice_groups": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                                                  I32P, I32P, I32P, I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                                  I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+                                                  ctypes.c_int64, I32P, I32P, I32P, I32P, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int), I32P, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int)]),
         "katsevich_project": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64, ctypes.c_int64,
                                              P]),
         "katsevich_sparse_upsample": (ctypes.c_int, [ctypes.POINTER(kats_geometry), P, P, ctypes.c_int64,
@@ -398,14 +399,15 @@ def katsevich_debug_fail_allocs(n: int) -> None:
     load().katsevich_debug_fail_allocs(n)
 
 
-def katsevich_slice_groups(s_begin: int, s_end: int, slices_per_pitch: int, max_groups: int = 4):
+def katsevich_slice_groups(s_begin: int, s_end: int, slices_per_pitch: int, max_groups: int = 4,
+                           lead_end: int = 2 ** 63 - 1):
     """The backprojection's slice grouping (host only): ([(groups, t, s0, cnt), ...], [(s, e), ...])."""
     cap = 4096
     arr = [(ctypes.c_int32 * cap)() for _ in range(4)]
     rest = (ctypes.c_int32 * (2 * cap))()
     ni, nr = ctypes.c_int(0), ctypes.c_int(0)
-    check(load().katsevich_slice_groups(s_begin, s_end, slices_per_pitch, max_groups, *arr, cap, ctypes.byref(ni),
-                                        rest, cap, ctypes.byref(nr)))
+    check(load().katsevich_slice_groups(s_begin, s_end, slices_per_pitch, max_groups, lead_end, *arr, cap,
+                                        ctypes.byref(ni), rest, cap, ctypes.byref(nr)))
     items = [tuple(int(a[i]) for a in arr) for i in range(ni.value)]
     return items, [(int(rest[2 * j]), int(rest[2 * j + 1])) for j in range(nr.value)]
 

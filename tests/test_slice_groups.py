@@ -69,3 +69,18 @@ def test_bad_arguments():
         with pytest.raises(native.KatsevichError) as e:
             native.katsevich_slice_groups(*args)
         assert e.value.status == native.KATS_EINVAL
+
+
+@pytest.mark.parametrize("S0,S1,N", [(80, 256, 70), (64, 256, 70), (0, 256, 70), (48, 194, 58), (16, 300, 7),
+                                     (0, 141, 70)])
+def test_groups_of_leads_partition_the_slab(S0, S1, N):
+    """The host pipeline's last slab in groups of leading slices [la, lb): each launch over [la, S1)
+    restricted to leads below lb.  Over any partition of the leads into such groups, every slice of
+    the slab is reconstructed exactly once."""
+    le = min(S0 + N, S1)
+    for cuts in ([S0, le], [S0, (S0 + le) // 2, le], list(range(S0, le, 5)) + [le]):
+        got = []
+        for la, lb in zip(cuts[:-1], cuts[1:]):
+            items, rest = native.katsevich_slice_groups(la, S1, N, 4, lb)
+            got += covered(items, rest, N)
+        assert sorted(got) == list(range(S0, S1)), cuts
