@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(B2_THREADS, 2)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == B2_CW;
-    const int tx = tid % B2_TX, ty = tid / B2_TX;  // consumers only
+    int tx, ty;  // consumers only
+    consumer_column(tid, &tx, &ty);
     int bx, by;
     cta_tile(&bx, &by);
     const int ix = bx * B2_TX + tx, iy = by * B2_TY + ty;
