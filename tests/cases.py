@@ -64,6 +64,17 @@ def fourpitch_case():
     return cfg, g, sino.astype(np.float32)
 
 
+def finevoxel_case():
+    """Config-1 scanner with 0.8 mm voxels on a 40 x 36 x 160 grid (60 slices per pitch, 2.7
+    pitches): three- and two-group items whose row bands scale with the voxel size."""
+    cfg = dict(synth.config(1))
+    cfg.update(nx=40, ny=36, nz=160, turns=6, voxel=0.8)
+    g = oracle.derive_geometry(cfg)
+    ell = synth.phantom_for(dict(cfg, phantom="shepp_style"), g, 79)
+    sino = synth.project(g, ell)
+    return cfg, g, sino.astype(np.float32)
+
+
 def odd_case():
     """Small geometry exercising every offset and parity: odd sizes, non-zero
     lambda0 / z0 / lambda_first / alpha and w offsets, odd n_psi, an axis voxel."""

@@ -58,6 +58,8 @@ for mode in (0, 1):
     run(f"multipitch{mode}", g, sino)
 _, g, sino = cases.fourpitch_case()
 run("fourpitch", g, sino, ("fp32", "fp16", "bf16"))
+_, g, sino = cases.finevoxel_case()
+run("finevoxel", g, sino, ("fp32", "bf16"))
 _, g, sino = cases.narrow_case()
 run("narrow", g, sino)
 _, g = cases.c3_small_case()
@@ -107,7 +109,7 @@ def test_checked_build_invariants_and_identity(tmp_path):
     assert checked["narrowed"] & 1 and checked["narrowed"] & 4  # backprojection and adjoint column checks
     assert plain["narrowed"] == 0
     names = sorted(os.listdir(dc))
-    assert names == sorted(os.listdir(dp)) and len(names) >= 20
+    assert names == sorted(os.listdir(dp)) and len(names) >= 23
     for n in names:
         a, b = np.load(dc / n), np.load(dp / n)
         if "adjoint" in n:  # window drains add with global float atomics: order varies run to run

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import c1_case, check32, fourpitch_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2, rows80_case, tall_case
+from cases import c1_case, check32, finevoxel_case, fourpitch_case, multipitch_case, narrow_case, near_tie, odd_case, rel_l2, rows80_case, tall_case
 
 pytestmark = pytest.mark.gpu
 
@@ -170,6 +170,19 @@ def test_fourpitch_bands(kats, torch):
     # slices [48, 194): leading slices 48-77 take three groups and 78-105 two, a different grouping
     slab = kp.recon_slab(dsino.clone(), 0, 48, 194).cpu().numpy()
     check32(slab, want[48:], name="slab 48-194")
+
+
+def test_fine_voxel_bands(kats, torch):
+    """Slice groups and row bands on 0.8 mm voxels (the band bound scales with dz and the voxel
+    spacing): FP32 against the oracle, and the 16-bit forms at their bar."""
+    _, g, sino = finevoxel_case()
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    assert kp.info["slices_per_pitch"] == 60
+    want = op.recon(sino.astype(np.float64))
+    dsino = torch.from_numpy(sino).cuda()
+    check32(kp.recon(dsino).cpu().numpy(), want)
+    for p in (kats.KATS_PREC_FP16, kats.KATS_PREC_BF16):
+        assert rel_l2(kp.recon(dsino, precision=p).cpu().numpy(), want) < 1e-3
 
 
 def test_odd_geometry_batch(kats, torch):
