@@ -75,11 +75,15 @@ def finevoxel_case():
     return cfg, g, sino.astype(np.float32)
 
 
-def odd_case():
+def odd_case(tall=False):
     """Small geometry exercising every offset and parity: odd sizes, non-zero
-    lambda0 / z0 / lambda_first / alpha and w offsets, odd n_psi, an axis voxel."""
+    lambda0 / z0 / lambda_first / alpha and w offsets, odd n_psi, an axis voxel.  tall: a 69-column
+    detector and 70 slices (22 per pitch), so that the slice-group backprojection takes four and
+    three groups with row bands under all the offsets."""
     cfg = dict(R=300.0, D=620.0, views_per_turn=90, turns=4, n_rows=13, n_cols=53, n_cols_full=53, col_keep=1,
                det_half_width=21.0, nx=21, ny=17, nz=23, voxel=1.5, pitch_factor=1.0, n_psi=31)
+    if tall:
+        cfg.update(turns=8, n_cols=69, n_cols_full=69, det_half_width=27.0, nz=70)
     g = oracle.derive_geometry(cfg)
     g.update(lambda0=0.7, z0=-4.0, lambda_first=0.11, alpha_offset=0.25 * g["d_alpha"], w_offset=0.3 * g["d_w"])
     # re-centre the volume in the (shifted) scan, keep z_first on the slice grid
@@ -87,7 +91,7 @@ def odd_case():
     h = g["P"] / (2 * math.pi)
     zc = g["z0"] + h * (g["lambda_first"] + 0.5 * g["n_views"] * dl)
     g["z_first"] = zc - 0.5 * (g["nz"] - 1) * g["dz"]
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(15 if tall else 5)
     sino = rng.normal(size=(g["n_views"], g["n_rows"], g["n_cols"]))
     return cfg, g, sino.astype(np.float32)
 

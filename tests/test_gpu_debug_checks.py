@@ -53,6 +53,8 @@ _, g, sino = cases.c1_case()
 run("c1", g, sino, ("fp32", "fp16", "bf16"))
 _, g, sino = cases.odd_case()
 run("odd", g, sino)
+_, g, sino = cases.odd_case(tall=True)
+run("odd_tall", g, sino, ("fp32", "fp16"))
 for mode in (0, 1):
     _, g, sino = cases.multipitch_case(mode)
     run(f"multipitch{mode}", g, sino)
@@ -109,7 +111,7 @@ def test_checked_build_invariants_and_identity(tmp_path):
     assert checked["narrowed"] & 1 and checked["narrowed"] & 4  # backprojection and adjoint column checks
     assert plain["narrowed"] == 0
     names = sorted(os.listdir(dc))
-    assert names == sorted(os.listdir(dp)) and len(names) >= 23
+    assert names == sorted(os.listdir(dp)) and len(names) >= 26
     for n in names:
         a, b = np.load(dc / n), np.load(dp / n)
         if "adjoint" in n:  # window drains add with global float atomics: order varies run to run

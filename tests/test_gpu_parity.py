@@ -185,6 +185,18 @@ def test_fine_voxel_bands(kats, torch):
         assert rel_l2(kp.recon(dsino, precision=p).cpu().numpy(), want) < 1e-3
 
 
+def test_odd_offsets_slice_groups(kats, torch):
+    """Every offset of the odd geometry (lambda0, z0, lambda_first, alpha and w) with a volume of
+    three pitches: four- and three-group items, row bands."""
+    _, g, sino = odd_case(tall=True)
+    op, kp = oracle.Plan(g), kats.Plan(g)
+    compare_tables(kp, op)
+    want = op.recon(sino.astype(np.float64))
+    dsino = torch.from_numpy(sino).cuda()
+    check32(kp.recon(dsino).cpu().numpy(), want)
+    assert rel_l2(kp.recon(dsino, precision=kats.KATS_PREC_FP16).cpu().numpy(), want) < 1e-3
+
+
 def test_odd_geometry_batch(kats, torch):
     _, g, sino = odd_case()
     op, kp = oracle.Plan(g), kats.Plan(g)
