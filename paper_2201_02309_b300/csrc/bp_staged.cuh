@@ -41,7 +41,7 @@ struct BPArgs {
     const float *w0, *w1;
     const float2 *trig, *trig_lo;
     int nx, ny, nz, N, vpt, n_rows, n_cols, gcols;
-    int s_begin, s_end;  // slices [s_begin, s_end) of this launch; s_begin a multiple of the z tile
+    int s_begin, s_end;  // slices [s_begin, s_end) of this launch (z tiles start at s_begin)
     // views [k_lo, k_hi] of this launch (backprojection only).  acc_in: the volume holds the raw
     // sums of the views below k_lo and the launch continues them; acc_final: scale and store the
     // result, else store raw sums for a later launch.  A split run adds every view in the order
